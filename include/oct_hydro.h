@@ -1,0 +1,179 @@
+/*
+ * oct_hydro.h -- C ABI of the GB300 (sm_103a) batched hydro right-hand side.
+ *
+ * The method is the hydro solver of Octo-Tiger (arXiv 2210.06439, Sec. II
+ * "Solvers"): finite volumes for the inviscid Euler equations with the
+ * Kurganov-Tadmor central flux, piecewise-parabolic reconstruction of the
+ * evolved variables to 26 points per cell, Newton-Cotes quadrature of the
+ * flux over each face; each kernel call works on sub-grids of 8^3 cells with
+ * their ghost layers (Sec. II "Data-Structure", Sec. III-D), and a time step
+ * takes three hydro iterations (Sec. V-B).  The paper gives no equations; the
+ * readings used here are:
+ *   - the conserved fields (rho, s_x, s_y, s_z, E_gas, tau, rho_1..rho_ns)
+ *     are reconstructed;
+ *   - PPM: Colella-Woodward 1984 interface values with monotonised-central
+ *     slopes and the CW84 monotonicity constraints;
+ *   - the 26 points are the 6 face centres, 12 edge midpoints and 8 corners of
+ *     a cell; the value at x + d/2 comes from 1-D PPM along cells x + m d;
+ *   - Newton-Cotes = tensor Simpson over the 3x3 points of a face (weights
+ *     16, 4, 1 over 36);
+ *   - KT flux with the local speed a_q = max(|v_n| + c) over both sides of
+ *     each quadrature point; a subgrid's a_max is the max over its faces;
+ *   - ideal gas with dual energy: e_int = E - |s|^2/(2 rho), replaced by
+ *     tau^gamma when e_int < de_switch1 * E;
+ *   - SSP-RK3 (Shu-Osher) with dt = cfl * min_s dx_s / a_max,s from the state
+ *     at the start of the step; after each stage rho >= rho_floor,
+ *     rho_i >= 0, tau re-synchronised when e_int > de_switch2 * E, tau >= 0.
+ *
+ * Data layout (all device pointers unless stated otherwise):
+ *   state U  : one ghosted block per subgrid, doubles, [field][z][y][x] with
+ *              B = edge + 6 cells per side (3 ghost layers), block s starting
+ *              at element offsets[s]; every offset a multiple of 4 (32 bytes).
+ *   dUdt     : interior only, doubles, [subgrid][field][z][y][x] with edge^3
+ *              cells per field, subgrids packed in index order.
+ *   neighbour table (host): 26 int32 per subgrid; direction (dx,dy,dz) in
+ *              {-1,0,1}^3 \ {0} at (dz+1)*9 + (dy+1)*3 + (dx+1), minus one
+ *              when that exceeds 13; -1 means a domain edge.
+ *
+ * Ownership: the caller owns every state, RHS and host buffer passed in.  The
+ * handle owns its scratch (the RK stage state, the RHS register, per-tile
+ * signal speeds, the dt slot, the work list, error flags) and its captured
+ * CUDA graphs; it allocates them with cudaMalloc on the current device at
+ * set-up and frees them in oct_hydro_destroy.
+ *
+ * Errors: every call returns an oct_status; nothing is thrown across the ABI.
+ * Arguments are validated on the host before any launch.  A non-physical
+ * state met on the device (rho <= 0 or a non-finite point value) sets a flag
+ * that oct_hydro_get_error_flags reads; no kernel traps.  oct_hydro_last_error
+ * gives the text of the calling thread's last failure.
+ *
+ * Streams: every call is ordered on the given CUDA stream (NULL = the legacy
+ * default stream).  Only the calls that return a value to the host
+ * (oct_hydro_max_dt, oct_hydro_rk_step with a non-NULL dt pointer,
+ * oct_hydro_get_error_flags, the *_host calls) synchronise that stream.
+ * A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef OCT_HYDRO_H
+#define OCT_HYDRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct oct_hydro *oct_hydro_t;
+
+typedef enum {
+    OCT_OK = 0,
+    OCT_E_ARG = -1,     /* invalid argument (size, pointer, alignment, value) */
+    OCT_E_CUDA = -2,    /* a CUDA runtime call failed                         */
+    OCT_E_NONPHYS = -3, /* a non-physical state was met on the device         */
+    OCT_E_TIMEOUT = -4, /* a bounded device wait ran out                      */
+    OCT_E_NOMEM = -5,   /* device or host allocation failed                   */
+    OCT_E_STATE = -6    /* call out of order (e.g. no layout set)             */
+} oct_status;
+
+typedef enum { OCT_FP64 = 0, OCT_MIXED = 1 } oct_precision;
+
+typedef enum { OCT_BC_GIVEN = 0, OCT_BC_PERIODIC = 1, OCT_BC_OUTFLOW = 2 } oct_bc;
+
+/* Device error flags (oct_hydro_get_error_flags). */
+#define OCT_FLAG_NONPHYS 0x1u /* rho <= 0 or non-finite value at a point   */
+#define OCT_FLAG_FLOOR 0x2u   /* a density, species or tau floor fired      */
+
+/* Creates a handle for n_subgrids subgrids (Sec. II "Data-Structure": one
+ * kernel invocation per set of subgrids with ghost layers).
+ *   edge      : 8, 12 or 16 for a uniform batch; 0 when per-subgrid edges are
+ *               given to oct_hydro_set_layout.
+ *   ghost     : number of ghost layers; must be 3.
+ *   n_species : 0..5 (fields = 6 + n_species).
+ *   gamma     : ratio of specific heats, > 1.
+ * For a uniform batch the default layout is packed blocks, dx = 1/edge per
+ * subgrid and ghosts given (OCT_BC_GIVEN).  Returns OCT_E_ARG for bad values,
+ * OCT_E_CUDA/OCT_E_NOMEM when the device cannot be set up; *out is NULL then.
+ */
+oct_status oct_hydro_create(int n_subgrids, int edge, int ghost, int n_species, double gamma, oct_hydro_t *out);
+
+/* Sets the batch layout; all pointers are HOST pointers and are copied.
+ *   edges      : n_subgrids edges in {8, 12, 16}; NULL = the create-time edge.
+ *   offsets    : n_subgrids state offsets in doubles (multiples of 4, blocks
+ *                not overlapping); NULL = packed in index order.
+ *   dx         : n_subgrids cell widths (> 0); NULL keeps the current ones.
+ *   level      : refinement levels (informational, may be NULL).
+ *   neighbours : 26 * n_subgrids int32 (see above); required when bc is
+ *                OCT_BC_PERIODIC or OCT_BC_OUTFLOW, which need one common edge.
+ *   bc         : oct_bc.
+ * Rebuilds the work list and drops captured graphs. */
+oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, const int64_t *offsets, const double *dx,
+                                const int32_t *level, const int32_t *neighbours, int bc);
+
+/* Numerical parameters: precision (oct_precision: FP64 everywhere, or
+ * reconstruction/flux arithmetic in FP32 with FP64 divergence, update,
+ * floors and dt), CFL number (0 < cfl <= 1, default 0.4), density floor
+ * (>= 0, default 1e-12) and the two dual-energy switches (default 1e-3 for
+ * the pressure recovery and 0.1 for the tau re-synchronisation). */
+oct_status oct_hydro_set_params(oct_hydro_t h, int precision, double cfl, double rho_floor, double de_switch1,
+                                double de_switch2);
+
+/* Caps dt in oct_hydro_rk_step (dt_cap > 0), e.g. to land on an output time;
+ * dt_cap <= 0 removes the cap. */
+oct_status oct_hydro_set_dt_cap(oct_hydro_t h, double dt_cap);
+
+/* Number of doubles of the state array the layout spans, and of dUdt. */
+int64_t oct_hydro_state_len(oct_hydro_t h);
+int64_t oct_hydro_rhs_len(oct_hydro_t h);
+
+/* One RHS evaluation (Sec. II "Solvers": the reconstruct and flux kernels
+ * plus the finite-volume divergence): reads U (ghosts used as they are),
+ * writes dUdt = -sum_k (F_k,+ - F_k,-)/dx for every interior cell and, when
+ * amax is not NULL, each subgrid's max signal speed (n_subgrids doubles).
+ * U and dUdt must not overlap. */
+oct_status oct_hydro_rhs(oct_hydro_t h, const double *U, double *dUdt, double *amax, void *cuda_stream);
+
+/* CFL time step of state U (Sec. V-A "determination of time-step size"):
+ * dt = cfl * min_s dx_s / a_max,s.  Writes it to *dt_host_out (host) and
+ * synchronises the stream. */
+oct_status oct_hydro_max_dt(oct_hydro_t h, const double *U, double *dt_host_out, void *cuda_stream);
+
+/* Fills the ghost layers of U on a uniform level from the neighbour table
+ * (periodic or outflow); does nothing for OCT_BC_GIVEN. */
+oct_status oct_hydro_fill_ghosts(oct_hydro_t h, double *U, void *cuda_stream);
+
+/* One SSP-RK3 time step in place (three hydro iterations per time step,
+ * Sec. V-B): dt from U's signal speeds, three RHS evaluations, combines,
+ * floors and dual-energy re-synchronisation, and a ghost fill after each
+ * stage (unless OCT_BC_GIVEN).  On entry U's ghosts must be valid.  The
+ * sequence is replayed from a CUDA graph captured on first use for this U.
+ * When dt_used_host_out is not NULL the stream is synchronised and the dt
+ * used is written there. */
+oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_used_host_out, void *cuda_stream);
+
+/* End-to-end variants on HOST buffers: copy the host state in, run n_steps
+ * RK3 steps (or one RHS), copy the result back.  U_host: oct_hydro_state_len
+ * doubles (page-locked memory gives full copy speed); dUdt_host:
+ * oct_hydro_rhs_len doubles.  The device copy of the state is owned by the
+ * handle.  Synchronous. */
+oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int n_steps, double *dt_last_out,
+                                   void *cuda_stream);
+oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_host, void *cuda_stream);
+
+/* Times the candidate launch shapes (tile shape, CTAs per SM) of the RHS
+ * kernel on U_sample and keeps the fastest for this layout and precision. */
+oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, void *cuda_stream);
+
+/* Reads and clears the device error flags (OCT_FLAG_*); synchronises. */
+oct_status oct_hydro_get_error_flags(oct_hydro_t h, uint32_t *flags);
+
+/* Text of the calling thread's last failed call ("" if none). */
+const char *oct_hydro_last_error(void);
+
+/* Releases the handle's device memory and graphs.  NULL is ignored. */
+void oct_hydro_destroy(oct_hydro_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCT_HYDRO_H */

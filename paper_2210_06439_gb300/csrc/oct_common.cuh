@@ -1,0 +1,114 @@
+// oct_common.cuh -- shared device definitions of the GB300 hydro kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace octh {
+
+constexpr int NG = 3;       // ghost layers
+constexpr int MAXNF = 11;   // 6 hydro fields + up to 5 species
+constexpr int MAXT = 8;     // max tile edge (x and y) of one work item
+constexpr int NTHREADS = 256;
+
+enum { F_RHO = 0, F_SX = 1, F_SY = 2, F_SZ = 3, F_EGAS = 4, F_TAU = 5, F_SPC = 6 };
+
+// One work item of the RHS kernel: a column of a subgrid, tx * ty cells in
+// x-y, all E cells in z (the kernel streams through z planes).
+struct WorkItem {
+    int s;        // subgrid index
+    int x0, y0;   // tile origin (interior coordinates)
+    int txty;     // tx | ty << 8
+};
+
+// Line groups: the 13 PPM lines grouped so that both sides of every face
+// quadrature point come from lines of one group (the L point of x-face point
+// (t1,t2) lies on line (1,t1,t2), the R point on line (1,-t1,-t2)).
+// Face point entries: axis, Simpson weight class, L (slot), R (slot); a slot
+// is 2*line+end (end 1 = the x + d/2 end of canonical line d, end 0 = x - d/2)
+// or, for the L side of a z face, 16 + index of the +z direction in the
+// saved-plane buffer ((dy+1)*3 + (dx+1)).
+struct GroupTab {
+    int nl;
+    int line[4][3];
+    int npt;
+    signed char axis[12], wcls[12], lslot[12], rslot[12];
+    int nzp;                       // +z ends this group leaves for the next plane
+    signed char zp_src[4], zp_dst[4];
+    int has[3];                    // group has lines with a nonzero x / y / z step
+};
+constexpr int NGROUPS = 7;
+
+struct RhsArgs {
+    const double *U;
+    double *dUdt;
+    double *amax_tile;             // per work item
+    const int *edge;
+    const long long *off;          // state offsets (doubles)
+    const long long *doff;         // RHS offsets (doubles)
+    const double *dx;
+    const WorkItem *items;
+    int n_items;
+    int nf;
+    double gamma, eps1;
+    unsigned *flags;
+};
+
+// ---------------------------------------------------------------------------
+// Exact conversions between FP64 and FP32 on the integer pipe.  On this GPU a
+// cvt between the two formats issues on the FP64 pipe (about 1/64 of the FP32
+// rate), so the mixed-precision kernels convert with integer operations
+// instead.  Both follow IEEE 754 binary64 <-> binary32 conversion with
+// round-to-nearest-even, including subnormals, infinities and NaN.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float d2f_rn(double d)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    int e = (int)((b >> 52) & 0x7FF);
+    unsigned long long m = b & 0x000FFFFFFFFFFFFFull;
+    int fe = e - 1023 + 127;
+    if (fe > 0 && fe < 255) {
+        // normal result: keep 23 bits, round the 29 dropped ones to even
+        unsigned int keep = (unsigned int)(m >> 29);
+        unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);
+        unsigned int r = ((unsigned int)fe << 23) | keep;
+        r += (rem > 0x10000000u) || (rem == 0x10000000u && (keep & 1u));
+        return __uint_as_float(sign | r);  // a carry into exponent 255 gives inf, as required
+    }
+    if (e == 0x7FF)
+        return __uint_as_float(sign | 0x7F800000u | (m ? 0x00400000u : 0u));
+    if (fe >= 255)
+        return __uint_as_float(sign | 0x7F800000u);
+    // subnormal or zero result
+    if (e == 0 || fe < -24)
+        return __uint_as_float(sign);
+    m |= 0x0010000000000000ull;
+    int sh = 29 + 1 - fe;  // 30..54
+    unsigned long long keep = m >> sh;
+    unsigned long long rem = m & ((1ull << sh) - 1);
+    unsigned long long half = 1ull << (sh - 1);
+    keep += (rem > half) || (rem == half && (keep & 1ull));
+    return __uint_as_float(sign | (unsigned int)keep);
+}
+
+__device__ __forceinline__ double f2d(float f)
+{
+    unsigned int b = __float_as_uint(f);
+    unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    unsigned int e = (b >> 23) & 0xFFu;
+    unsigned long long m = b & 0x7FFFFFu;
+    if (e != 0 && e != 0xFF)
+        return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | (m << 29)));
+    if (e == 0xFF)
+        return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | (m << 29)));
+    if (m == 0)
+        return __longlong_as_double((long long)sign);
+    // subnormal float: normalise
+    int lz = __clz((int)(m << 9));  // leading zeros within the 23-bit field
+    m <<= (lz + 1);
+    m &= 0x7FFFFFu;
+    int ee = 1 - 127 - (lz + 1) + 1023;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)ee << 52) | (m << 29)));
+}
+
+}  // namespace octh

@@ -1,0 +1,781 @@
+// oct_hydro.cu -- host side of the C ABI declared in include/oct_hydro.h:
+// handle, validation, work list, launches, the RK3 CUDA graph and the
+// autotuner.  The kernels live in rhs_kernel.cuh and step_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/oct_hydro.h"
+#include "oct_common.cuh"
+#include "rhs_kernel.cuh"
+#include "step_kernels.cuh"
+
+using namespace octh;
+
+static thread_local std::string g_last_error;
+
+static oct_status fail(oct_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                                   \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? OCT_E_NOMEM : OCT_E_CUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                     \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Line-group tables (see rhs_kernel.cuh)
+// ---------------------------------------------------------------------------
+static void canon(const int *d, int *line, int *end)
+{
+    int first = d[0] ? d[0] : (d[1] ? d[1] : d[2]);
+    int sg = first > 0 ? 1 : -1;
+    for (int a = 0; a < 3; a++)
+        line[a] = d[a] * sg;
+    *end = first > 0 ? 1 : 0;
+}
+
+static std::vector<GroupTab> build_groups()
+{
+    static const int L[13][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1},
+                                 {0, 1, 1}, {0, 1, -1}, {1, 1, 1}, {1, -1, -1}, {1, -1, 1}, {1, 1, -1}};
+    static const int GL[NGROUPS][5] = {{1, 0}, {1, 1}, {1, 2}, {2, 3, 4}, {2, 5, 6}, {2, 7, 8}, {4, 9, 10, 11, 12}};
+    std::vector<GroupTab> gs(NGROUPS);
+    for (int g = 0; g < NGROUPS; g++) {
+        GroupTab &G = gs[g];
+        memset(&G, 0, sizeof G);
+        G.nl = GL[g][0];
+        for (int l = 0; l < G.nl; l++)
+            for (int a = 0; a < 3; a++) {
+                G.line[l][a] = L[GL[g][1 + l]][a];
+                if (G.line[l][a])
+                    G.has[a] = 1;
+            }
+        auto find = [&](const int *d) -> int {
+            int ln[3], e;
+            canon(d, ln, &e);
+            for (int l = 0; l < G.nl; l++)
+                if (ln[0] == G.line[l][0] && ln[1] == G.line[l][1] && ln[2] == G.line[l][2])
+                    return 2 * l + e;
+            return -1;
+        };
+        for (int k = 0; k < 3; k++) {
+            int a1 = (k == 0) ? 1 : 0, a2 = (k == 2) ? 1 : 2;
+            for (int t2 = -1; t2 <= 1; t2++)
+                for (int t1 = -1; t1 <= 1; t1++) {
+                    int dL[3] = {0, 0, 0}, dR[3] = {0, 0, 0};
+                    dL[k] = 1;
+                    dR[k] = -1;
+                    dL[a1] = dR[a1] = t1;
+                    dL[a2] = dR[a2] = t2;
+                    int ls = find(dL), rs = find(dR);
+                    if (ls < 0 || rs < 0)
+                        continue;
+                    int p = G.npt++;
+                    G.axis[p] = (signed char)k;
+                    G.wcls[p] = (signed char)((t1 != 0) + (t2 != 0));
+                    G.rslot[p] = (signed char)rs;
+                    G.lslot[p] = (signed char)(k == 2 ? 16 + (t2 + 1) * 3 + (t1 + 1) : ls);
+                }
+        }
+        for (int l = 0; l < G.nl; l++) {
+            if (!G.line[l][2])
+                continue;
+            int end = G.line[l][2] > 0 ? 1 : 0;
+            int sg = end ? 1 : -1;
+            int dxe = G.line[l][0] * sg, dye = G.line[l][1] * sg;
+            G.zp_src[G.nzp] = (signed char)(2 * l + end);
+            G.zp_dst[G.nzp] = (signed char)((dye + 1) * 3 + (dxe + 1));
+            G.nzp++;
+        }
+    }
+    return gs;
+}
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct oct_hydro {
+    int device = 0, n_sm = 0;
+    int n_sub = 0, edge0 = 0, n_species = 0, nf = 0;
+    double gamma = 5.0 / 3.0;
+    int precision = OCT_FP64;
+    double cfl = 0.4, rho_floor = 1e-12, eps1 = 1e-3, eps2 = 0.1, dt_cap = 0.0;
+    int bc = OCT_BC_GIVEN;
+    bool layout_ok = false;
+    // host copies
+    std::vector<int> edge;
+    std::vector<long long> off, doff;
+    std::vector<double> dx;
+    std::vector<int> nbr;
+    std::vector<WorkItem> items;
+    std::vector<int> item_begin;
+    long long state_len = 0, rhs_len = 0;
+    int tile_mode = 0;       // 0: 8x8 (6x6 for edge 12); 1: 8x4 split
+    int ctas_per_sm[2] = {0, 0};
+    // device memory
+    int *d_edge = nullptr, *d_nbr = nullptr, *d_item_begin = nullptr;
+    long long *d_off = nullptr, *d_doff = nullptr;
+    double *d_dx = nullptr;
+    WorkItem *d_items = nullptr;
+    double *d_amax_tile = nullptr, *d_dt = nullptr, *d_W = nullptr, *d_L = nullptr, *d_Uhost = nullptr,
+           *d_Lhost = nullptr;
+    unsigned *d_flags = nullptr;
+    std::map<const double *, GraphEntry> graphs;
+};
+
+static bool g_tables_ready[64];
+
+static oct_status ensure_tables(int dev)
+{
+    if (dev >= 0 && dev < 64 && g_tables_ready[dev])
+        return OCT_OK;
+    std::vector<GroupTab> gs = build_groups();
+    CUDA_TRY(cudaMemcpyToSymbol(c_groups, gs.data(), sizeof(GroupTab) * NGROUPS));
+    for (int T = 0; T < 2; T++) {
+        (void)T;
+    }
+    if (dev >= 0 && dev < 64)
+        g_tables_ready[dev] = true;
+    return OCT_OK;
+}
+
+template <class P>
+static void dfree(P *&p)
+{
+    if (p)
+        cudaFree((void *)p);
+    p = nullptr;
+}
+
+static void drop_graphs(oct_hydro *h)
+{
+    for (auto &kv : h->graphs)
+        if (kv.second.exec)
+            cudaGraphExecDestroy(kv.second.exec);
+    h->graphs.clear();
+}
+
+static void free_layout(oct_hydro *h)
+{
+    dfree(h->d_edge);
+    dfree(h->d_nbr);
+    dfree(h->d_item_begin);
+    dfree(h->d_off);
+    dfree(h->d_doff);
+    dfree(h->d_dx);
+    dfree(h->d_items);
+    dfree(h->d_amax_tile);
+    dfree(h->d_W);
+    dfree(h->d_L);
+    dfree(h->d_Uhost);
+    dfree(h->d_Lhost);
+    drop_graphs(h);
+}
+
+static size_t rhs_smem(const oct_hydro *h, int prec)
+{
+    return smem_plan(h->nf, prec == OCT_FP64 ? 8 : 4, prec != OCT_FP64).total;
+}
+
+static oct_status set_kernel_attrs(oct_hydro *h)
+{
+    for (int prec = 0; prec < 2; prec++) {
+        size_t sm = rhs_smem(h, prec);
+        const void *fn = prec == OCT_FP64 ? (const void *)rhs_kernel<double, false> : (const void *)rhs_kernel<float, true>;
+        CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int nb = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NTHREADS, sm));
+        if (nb < 1)
+            return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM (%zu bytes shared memory)", sm);
+        h->ctas_per_sm[prec] = nb;
+    }
+    return OCT_OK;
+}
+
+static void build_items(oct_hydro *h)
+{
+    h->items.clear();
+    h->item_begin.assign(h->n_sub + 1, 0);
+    for (int s = 0; s < h->n_sub; s++) {
+        h->item_begin[s] = (int)h->items.size();
+        int E = h->edge[s];
+        int tx, ty;
+        if (E == 12) {
+            tx = ty = 6;
+        } else {
+            tx = ty = 8;
+            if (h->tile_mode == 1)
+                ty = 4;
+        }
+        for (int y0 = 0; y0 < E; y0 += ty)
+            for (int x0 = 0; x0 < E; x0 += tx) {
+                WorkItem w;
+                w.s = s;
+                w.x0 = x0;
+                w.y0 = y0;
+                w.txty = tx | (ty << 8);
+                h->items.push_back(w);
+            }
+    }
+    h->item_begin[h->n_sub] = (int)h->items.size();
+}
+
+static oct_status upload_items(oct_hydro *h)
+{
+    dfree(h->d_items);
+    dfree(h->d_item_begin);
+    dfree(h->d_amax_tile);
+    CUDA_TRY(cudaMalloc(&h->d_items, sizeof(WorkItem) * h->items.size()));
+    CUDA_TRY(cudaMemcpy(h->d_items, h->items.data(), sizeof(WorkItem) * h->items.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&h->d_item_begin, sizeof(int) * h->item_begin.size()));
+    CUDA_TRY(cudaMemcpy(h->d_item_begin, h->item_begin.data(), sizeof(int) * h->item_begin.size(),
+                        cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&h->d_amax_tile, sizeof(double) * std::max<size_t>(1, h->items.size())));
+    return OCT_OK;
+}
+
+static bool valid_edge(int E)
+{
+    return E == 8 || E == 12 || E == 16;
+}
+
+extern "C" oct_status oct_hydro_create(int n_subgrids, int edge, int ghost, int n_species, double gamma,
+                                       oct_hydro_t *out)
+{
+    if (!out)
+        return fail(OCT_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_subgrids <= 0)
+        return fail(OCT_E_ARG, "n_subgrids must be positive (got %d)", n_subgrids);
+    if (edge != 0 && !valid_edge(edge))
+        return fail(OCT_E_ARG, "edge must be 8, 12, 16 or 0 (got %d)", edge);
+    if (ghost != NG)
+        return fail(OCT_E_ARG, "ghost must be 3 (got %d)", ghost);
+    if (n_species < 0 || n_species > MAXNF - 6)
+        return fail(OCT_E_ARG, "n_species must be in 0..%d (got %d)", MAXNF - 6, n_species);
+    if (!(gamma > 1.0) || !std::isfinite(gamma))
+        return fail(OCT_E_ARG, "gamma must be > 1 (got %g)", gamma);
+    oct_hydro *h = new (std::nothrow) oct_hydro;
+    if (!h)
+        return fail(OCT_E_NOMEM, "host allocation failed");
+    h->n_sub = n_subgrids;
+    h->edge0 = edge;
+    h->n_species = n_species;
+    h->nf = 6 + n_species;
+    h->gamma = gamma;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(OCT_E_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    oct_status st = ensure_tables(h->device);
+    if (st == OCT_OK)
+        st = set_kernel_attrs(h);
+    if (st == OCT_OK && cudaMalloc(&h->d_flags, sizeof(unsigned)) != cudaSuccess)
+        st = fail(OCT_E_NOMEM, "cudaMalloc flags");
+    if (st == OCT_OK && cudaMemset(h->d_flags, 0, sizeof(unsigned)) != cudaSuccess)
+        st = fail(OCT_E_CUDA, "cudaMemset flags");
+    if (st == OCT_OK && cudaMalloc(&h->d_dt, sizeof(double)) != cudaSuccess)
+        st = fail(OCT_E_NOMEM, "cudaMalloc dt");
+    if (st != OCT_OK) {
+        oct_hydro_destroy(h);
+        return st;
+    }
+    if (edge != 0) {
+        std::vector<double> dxv(n_subgrids, 1.0 / edge);
+        st = oct_hydro_set_layout(h, nullptr, nullptr, dxv.data(), nullptr, nullptr, OCT_BC_GIVEN);
+        if (st != OCT_OK) {
+            std::string keep = g_last_error;
+            oct_hydro_destroy(h);
+            g_last_error = keep;
+            return st;
+        }
+    }
+    *out = h;
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, const int64_t *offsets,
+                                           const double *dx, const int32_t *level, const int32_t *neighbours, int bc)
+{
+    (void)level;
+    if (!h)
+        return fail(OCT_E_ARG, "handle is NULL");
+    if (bc < OCT_BC_GIVEN || bc > OCT_BC_OUTFLOW)
+        return fail(OCT_E_ARG, "bc must be 0, 1 or 2 (got %d)", bc);
+    const int n = h->n_sub;
+    std::vector<int> edge(n);
+    for (int s = 0; s < n; s++) {
+        edge[s] = edges ? edges[s] : h->edge0;
+        if (!valid_edge(edge[s]))
+            return fail(OCT_E_ARG, "edge of subgrid %d must be 8, 12 or 16 (got %d)", s, edge[s]);
+    }
+    if (!dx && (h->dx.size() != (size_t)n))
+        return fail(OCT_E_ARG, "dx is required");
+    std::vector<double> dxv(n);
+    for (int s = 0; s < n; s++) {
+        dxv[s] = dx ? dx[s] : h->dx[s];
+        if (!(dxv[s] > 0.0) || !std::isfinite(dxv[s]))
+            return fail(OCT_E_ARG, "dx of subgrid %d must be positive (got %g)", s, dxv[s]);
+    }
+    const int nf = h->nf;
+    std::vector<long long> off(n), doff(n);
+    long long state_len = 0, rhs_len = 0;
+    std::vector<std::pair<long long, long long>> spans(n);
+    for (int s = 0; s < n; s++) {
+        long long B = edge[s] + 2 * NG;
+        long long len = nf * B * B * B;
+        if (offsets) {
+            off[s] = offsets[s];
+            if (off[s] < 0 || off[s] % 4 != 0)
+                return fail(OCT_E_ARG, "offset of subgrid %d must be a non-negative multiple of 4 doubles (got %lld)",
+                            s, (long long)off[s]);
+        } else {
+            off[s] = state_len;
+        }
+        spans[s] = {off[s], off[s] + len};
+        state_len = std::max(state_len, off[s] + len);
+        if (!offsets)
+            state_len = (state_len + 3) / 4 * 4;
+        doff[s] = rhs_len;
+        rhs_len += nf * (long long)edge[s] * edge[s] * edge[s];
+    }
+    std::sort(spans.begin(), spans.end());
+    for (int s = 1; s < n; s++)
+        if (spans[s].first < spans[s - 1].second)
+            return fail(OCT_E_ARG, "subgrid blocks overlap in the state array");
+    std::vector<int> nb;
+    if (bc != OCT_BC_GIVEN) {
+        if (!neighbours)
+            return fail(OCT_E_ARG, "a neighbour table is required for periodic/outflow ghosts");
+        for (int s = 1; s < n; s++)
+            if (edge[s] != edge[0])
+                return fail(OCT_E_ARG, "ghost exchange needs one common edge");
+        nb.assign(neighbours, neighbours + 26 * (size_t)n);
+        for (size_t i = 0; i < nb.size(); i++)
+            if (nb[i] < -1 || nb[i] >= n)
+                return fail(OCT_E_ARG, "neighbour entry %zu out of range (%d)", i, nb[i]);
+    }
+    // commit
+    free_layout(h);
+    h->layout_ok = false;
+    h->edge = edge;
+    h->dx = dxv;
+    h->off = off;
+    h->doff = doff;
+    h->nbr = nb;
+    h->bc = bc;
+    h->state_len = state_len;
+    h->rhs_len = rhs_len;
+    build_items(h);
+    CUDA_TRY(cudaMalloc(&h->d_edge, sizeof(int) * n));
+    CUDA_TRY(cudaMemcpy(h->d_edge, edge.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&h->d_dx, sizeof(double) * n));
+    CUDA_TRY(cudaMemcpy(h->d_dx, dxv.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&h->d_off, sizeof(long long) * n));
+    CUDA_TRY(cudaMemcpy(h->d_off, off.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&h->d_doff, sizeof(long long) * n));
+    CUDA_TRY(cudaMemcpy(h->d_doff, doff.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
+    if (!nb.empty()) {
+        CUDA_TRY(cudaMalloc(&h->d_nbr, sizeof(int) * nb.size()));
+        CUDA_TRY(cudaMemcpy(h->d_nbr, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice));
+    }
+    oct_status st = upload_items(h);
+    if (st != OCT_OK)
+        return st;
+    h->layout_ok = true;
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_set_params(oct_hydro_t h, int precision, double cfl, double rho_floor,
+                                           double de_switch1, double de_switch2)
+{
+    if (!h)
+        return fail(OCT_E_ARG, "handle is NULL");
+    if (precision != OCT_FP64 && precision != OCT_MIXED)
+        return fail(OCT_E_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+    if (!(cfl > 0.0 && cfl <= 1.0))
+        return fail(OCT_E_ARG, "cfl must be in (0, 1] (got %g)", cfl);
+    if (!(rho_floor >= 0.0) || !std::isfinite(rho_floor))
+        return fail(OCT_E_ARG, "rho_floor must be >= 0");
+    if (!(de_switch1 >= 0.0 && de_switch1 < 1.0) || !(de_switch2 >= 0.0 && de_switch2 < 1.0))
+        return fail(OCT_E_ARG, "dual-energy switches must be in [0, 1)");
+    h->precision = precision;
+    h->cfl = cfl;
+    h->rho_floor = rho_floor;
+    h->eps1 = de_switch1;
+    h->eps2 = de_switch2;
+    drop_graphs(h);
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_set_dt_cap(oct_hydro_t h, double dt_cap)
+{
+    if (!h)
+        return fail(OCT_E_ARG, "handle is NULL");
+    if (std::isnan(dt_cap))
+        return fail(OCT_E_ARG, "dt_cap is NaN");
+    h->dt_cap = dt_cap;
+    drop_graphs(h);
+    return OCT_OK;
+}
+
+extern "C" int64_t oct_hydro_state_len(oct_hydro_t h)
+{
+    return h && h->layout_ok ? h->state_len : -1;
+}
+
+extern "C" int64_t oct_hydro_rhs_len(oct_hydro_t h)
+{
+    return h && h->layout_ok ? h->rhs_len : -1;
+}
+
+static oct_status check_ready(oct_hydro *h)
+{
+    if (!h)
+        return fail(OCT_E_ARG, "handle is NULL");
+    if (!h->layout_ok)
+        return fail(OCT_E_STATE, "no layout set");
+    return OCT_OK;
+}
+
+static oct_status check_ptr(const void *p, const char *name)
+{
+    if (!p)
+        return fail(OCT_E_ARG, "%s is NULL", name);
+    if ((uintptr_t)p % 16 != 0)
+        return fail(OCT_E_ARG, "%s must be 16-byte aligned", name);
+    return OCT_OK;
+}
+
+// Launches the RHS kernel of the handle's precision.
+static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaStream_t st)
+{
+    RhsArgs A;
+    A.U = U;
+    A.dUdt = dUdt;
+    A.amax_tile = h->d_amax_tile;
+    A.edge = h->d_edge;
+    A.off = h->d_off;
+    A.doff = h->d_doff;
+    A.dx = h->d_dx;
+    A.items = h->d_items;
+    A.n_items = (int)h->items.size();
+    A.nf = h->nf;
+    A.gamma = h->gamma;
+    A.eps1 = h->eps1;
+    A.flags = h->d_flags;
+    int prec = h->precision;
+    int grid = std::min<int>(A.n_items, h->n_sm * h->ctas_per_sm[prec]);
+    size_t sm = rhs_smem(h, prec);
+    if (prec == OCT_FP64)
+        rhs_kernel<double, false><<<grid, NTHREADS, sm, st>>>(A);
+    else
+        rhs_kernel<float, true><<<grid, NTHREADS, sm, st>>>(A);
+    CUDA_TRY(cudaGetLastError());
+    return OCT_OK;
+}
+
+static oct_status ensure_scratch(oct_hydro *h)
+{
+    if (!h->d_L)
+        CUDA_TRY(cudaMalloc(&h->d_L, sizeof(double) * std::max<long long>(1, h->rhs_len)));
+    if (!h->d_W)
+        CUDA_TRY(cudaMalloc(&h->d_W, sizeof(double) * std::max<long long>(1, h->state_len)));
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_rhs(oct_hydro_t h, const double *U, double *dUdt, double *amax, void *cuda_stream)
+{
+    oct_status st = check_ready(h);
+    if (st != OCT_OK)
+        return st;
+    if ((st = check_ptr(U, "U")) != OCT_OK || (st = check_ptr(dUdt, "dUdt")) != OCT_OK)
+        return st;
+    const char *u0 = (const char *)U, *u1 = u0 + h->state_len * 8;
+    const char *d0 = (const char *)dUdt, *d1 = d0 + h->rhs_len * 8;
+    if (u0 < d1 && d0 < u1)
+        return fail(OCT_E_ARG, "U and dUdt overlap");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if ((st = launch_rhs(h, U, dUdt, s)) != OCT_OK)
+        return st;
+    if (amax) {
+        amax_subgrid_kernel<<<(h->n_sub + 255) / 256, 256, 0, s>>>(h->n_sub, h->d_item_begin, h->d_amax_tile, amax);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return OCT_OK;
+}
+
+static oct_status launch_dt(oct_hydro *h, cudaStream_t s)
+{
+    dt_kernel<<<1, 1024, 0, s>>>((int)h->items.size(), h->d_items, h->d_dx, h->d_amax_tile, h->cfl, h->dt_cap,
+                                 h->d_dt);
+    CUDA_TRY(cudaGetLastError());
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_max_dt(oct_hydro_t h, const double *U, double *dt_host_out, void *cuda_stream)
+{
+    oct_status st = check_ready(h);
+    if (st != OCT_OK)
+        return st;
+    if ((st = check_ptr(U, "U")) != OCT_OK)
+        return st;
+    if (!dt_host_out)
+        return fail(OCT_E_ARG, "dt_host_out is NULL");
+    if ((st = ensure_scratch(h)) != OCT_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if ((st = launch_rhs(h, U, h->d_L, s)) != OCT_OK)
+        return st;
+    double cap = h->dt_cap;
+    h->dt_cap = 0.0;
+    st = launch_dt(h, s);
+    h->dt_cap = cap;
+    if (st != OCT_OK)
+        return st;
+    CUDA_TRY(cudaMemcpyAsync(dt_host_out, h->d_dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return OCT_OK;
+}
+
+static oct_status launch_ghosts(oct_hydro *h, double *U, cudaStream_t s)
+{
+    if (h->bc == OCT_BC_GIVEN)
+        return OCT_OK;
+    ghost_fill_kernel<<<h->n_sub, 256, 0, s>>>(U, h->edge[0], h->d_off, h->nf, h->d_nbr, h->d_flags);
+    CUDA_TRY(cudaGetLastError());
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_fill_ghosts(oct_hydro_t h, double *U, void *cuda_stream)
+{
+    oct_status st = check_ready(h);
+    if (st != OCT_OK)
+        return st;
+    if ((st = check_ptr(U, "U")) != OCT_OK)
+        return st;
+    return launch_ghosts(h, U, (cudaStream_t)cuda_stream);
+}
+
+static oct_status launch_combine(oct_hydro *h, int stage, const double *U0, const double *X, double *out,
+                                 cudaStream_t s)
+{
+    CombineArgs A;
+    A.stage = stage;
+    A.U0 = U0;
+    A.X = X;
+    A.out = out;
+    A.L = h->d_L;
+    A.dt = h->d_dt;
+    A.edge = h->d_edge;
+    A.off = h->d_off;
+    A.doff = h->d_doff;
+    A.nf = h->nf;
+    A.gamma = h->gamma;
+    A.rho_floor = h->rho_floor;
+    A.eps2 = h->eps2;
+    A.flags = h->d_flags;
+    combine_kernel<<<h->n_sub, 256, 0, s>>>(A);
+    CUDA_TRY(cudaGetLastError());
+    return OCT_OK;
+}
+
+// The launches of one SSP-RK3 step on U (W: stage state, L: RHS register).
+static oct_status enqueue_step(oct_hydro *h, double *U, cudaStream_t s)
+{
+    oct_status st;
+    double *W = h->d_W;
+    if (h->bc == OCT_BC_GIVEN)
+        CUDA_TRY(cudaMemcpyAsync(W, U, sizeof(double) * h->state_len, cudaMemcpyDeviceToDevice, s));
+    if ((st = launch_rhs(h, U, h->d_L, s)) != OCT_OK) return st;
+    if ((st = launch_dt(h, s)) != OCT_OK) return st;
+    if ((st = launch_combine(h, 1, U, U, W, s)) != OCT_OK) return st;
+    if ((st = launch_ghosts(h, W, s)) != OCT_OK) return st;
+    if ((st = launch_rhs(h, W, h->d_L, s)) != OCT_OK) return st;
+    if ((st = launch_combine(h, 2, U, W, W, s)) != OCT_OK) return st;
+    if ((st = launch_ghosts(h, W, s)) != OCT_OK) return st;
+    if ((st = launch_rhs(h, W, h->d_L, s)) != OCT_OK) return st;
+    if ((st = launch_combine(h, 3, U, W, U, s)) != OCT_OK) return st;
+    if ((st = launch_ghosts(h, U, s)) != OCT_OK) return st;
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_used_host_out, void *cuda_stream)
+{
+    oct_status st = check_ready(h);
+    if (st != OCT_OK)
+        return st;
+    if ((st = check_ptr(U, "U")) != OCT_OK)
+        return st;
+    if ((st = ensure_scratch(h)) != OCT_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    GraphEntry &ge = h->graphs[U];
+    if (!ge.exec && s != 0) {
+        cudaGraph_t graph;
+        CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        st = enqueue_step(h, U, s);
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (st != OCT_OK)
+            return st;
+        if (e != cudaSuccess)
+            return fail(OCT_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            ge.exec = nullptr;
+            return fail(OCT_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        }
+    }
+    if (ge.exec) {
+        CUDA_TRY(cudaGraphLaunch(ge.exec, s));
+    } else if ((st = enqueue_step(h, U, s)) != OCT_OK) {
+        return st;
+    }
+    if (dt_used_host_out) {
+        CUDA_TRY(cudaMemcpyAsync(dt_used_host_out, h->d_dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int n_steps, double *dt_last_out,
+                                              void *cuda_stream)
+{
+    oct_status st = check_ready(h);
+    if (st != OCT_OK)
+        return st;
+    if (!U_host)
+        return fail(OCT_E_ARG, "U_host is NULL");
+    if (n_steps < 0)
+        return fail(OCT_E_ARG, "n_steps must be >= 0");
+    if (!h->d_Uhost)
+        CUDA_TRY(cudaMalloc(&h->d_Uhost, sizeof(double) * h->state_len));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    size_t bytes = sizeof(double) * h->state_len;
+    CUDA_TRY(cudaMemcpyAsync(h->d_Uhost, U_host, bytes, cudaMemcpyHostToDevice, s));
+    for (int i = 0; i < n_steps; i++)
+        if ((st = oct_hydro_rk_step(h, h->d_Uhost, nullptr, cuda_stream)) != OCT_OK)
+            return st;
+    CUDA_TRY(cudaMemcpyAsync(U_host, h->d_Uhost, bytes, cudaMemcpyDeviceToHost, s));
+    if (dt_last_out)
+        CUDA_TRY(cudaMemcpyAsync(dt_last_out, h->d_dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_host, void *cuda_stream)
+{
+    oct_status st = check_ready(h);
+    if (st != OCT_OK)
+        return st;
+    if (!U_host || !dUdt_host)
+        return fail(OCT_E_ARG, "host buffer is NULL");
+    if (!h->d_Uhost)
+        CUDA_TRY(cudaMalloc(&h->d_Uhost, sizeof(double) * h->state_len));
+    if (!h->d_Lhost)
+        CUDA_TRY(cudaMalloc(&h->d_Lhost, sizeof(double) * std::max<long long>(1, h->rhs_len)));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    CUDA_TRY(cudaMemcpyAsync(h->d_Uhost, U_host, sizeof(double) * h->state_len, cudaMemcpyHostToDevice, s));
+    if ((st = launch_rhs(h, h->d_Uhost, h->d_Lhost, s)) != OCT_OK)
+        return st;
+    CUDA_TRY(cudaMemcpyAsync(dUdt_host, h->d_Lhost, sizeof(double) * h->rhs_len, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, void *cuda_stream)
+{
+    oct_status st = check_ready(h);
+    if (st != OCT_OK)
+        return st;
+    if ((st = check_ptr(U_sample, "U_sample")) != OCT_OK)
+        return st;
+    if ((st = ensure_scratch(h)) != OCT_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_mode = h->tile_mode;
+    for (int mode = 0; mode < 2; mode++) {
+        h->tile_mode = mode;
+        build_items(h);
+        if ((st = upload_items(h)) != OCT_OK)
+            return st;
+        float tot = 0.0f;
+        for (int rep = 0; rep < 4; rep++) {
+            CUDA_TRY(cudaEventRecord(e0, s));
+            if ((st = launch_rhs(h, U_sample, h->d_L, s)) != OCT_OK)
+                return st;
+            CUDA_TRY(cudaEventRecord(e1, s));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0)
+                tot += ms;
+        }
+        if (tot < best) {
+            best = tot;
+            best_mode = mode;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->tile_mode = best_mode;
+    build_items(h);
+    drop_graphs(h);
+    return upload_items(h);
+}
+
+extern "C" oct_status oct_hydro_get_error_flags(oct_hydro_t h, uint32_t *flags)
+{
+    if (!h || !flags)
+        return fail(OCT_E_ARG, "handle or flags is NULL");
+    unsigned v = 0;
+    CUDA_TRY(cudaMemcpy(&v, h->d_flags, sizeof v, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(h->d_flags, 0, sizeof v));
+    *flags = v;
+    return OCT_OK;
+}
+
+extern "C" const char *oct_hydro_last_error(void)
+{
+    return g_last_error.c_str();
+}
+
+extern "C" void oct_hydro_destroy(oct_hydro_t h)
+{
+    if (!h)
+        return;
+    free_layout(h);
+    dfree(h->d_flags);
+    dfree(h->d_dt);
+    delete h;
+}

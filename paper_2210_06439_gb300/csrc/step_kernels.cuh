@@ -1,0 +1,179 @@
+// step_kernels.cuh -- the memory-bound kernels around the RHS: per-subgrid
+// signal-speed reduction, the CFL dt reduction, the SSP-RK3 combine with
+// floors and dual-energy re-synchronisation, and the uniform-level ghost fill.
+#pragma once
+#include "oct_common.cuh"
+
+namespace octh {
+
+// a_max of each subgrid = max over its work items (the items of subgrid s
+// are item_begin[s] .. item_begin[s+1]-1).
+__global__ void amax_subgrid_kernel(int n_sub, const int *item_begin, const double *amax_tile, double *amax)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sub)
+        return;
+    double m = 0.0;
+    for (int t = item_begin[s]; t < item_begin[s + 1]; t++)
+        m = fmax(m, amax_tile[t]);
+    amax[s] = m;
+}
+
+// dt = cfl * min over items of dx_s / a_max,item (Sec. V-A, time-step size);
+// min_t dx/a_t = dx / max_t a_t exactly because correctly rounded division is
+// monotone.  One block of 1024 threads; writes dt[0].
+__global__ void dt_kernel(int n_items, const WorkItem *items, const double *dx, const double *amax_tile, double cfl,
+                          double dt_cap, double *dt)
+{
+    __shared__ double red[32];
+    double m = INFINITY;
+    for (int t = threadIdx.x; t < n_items; t += blockDim.x)
+        m = fmin(m, dx[items[t].s] / amax_tile[t]);
+    for (int o = 16; o > 0; o >>= 1)
+        m = fmin(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : INFINITY;
+        for (int o = 16; o > 0; o >>= 1)
+            m = fmin(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        if (threadIdx.x == 0) {
+            double d = cfl * m;
+            if (dt_cap > 0.0 && dt_cap < d)
+                d = dt_cap;
+            dt[0] = d;
+        }
+    }
+}
+
+struct CombineArgs {
+    int stage;            // 1, 2, 3
+    const double *U0;     // state at the start of the step (ghosted layout)
+    const double *X;      // stage input (ghosted layout)
+    double *out;          // stage output (ghosted layout); may alias X
+    const double *L;      // RHS of X (RHS layout)
+    const double *dt;     // device scalar
+    const int *edge;
+    const long long *off, *doff;
+    int nf;
+    double gamma, rho_floor, eps2;
+    unsigned *flags;
+};
+
+// One SSP-RK3 combine (Shu-Osher) on the interior, one block per subgrid:
+//   stage 1: out = X + dt L                     (X = U0)
+//   stage 2: out = 3/4 U0 + 1/4 (X + dt L)
+//   stage 3: out = 1/3 U0 + 2/3 (X + dt L)
+// then the floors rho >= rho_floor, rho_i >= 0, the tau re-synchronisation
+// tau = e_int^(1/gamma) where e_int = E - |s|^2/(2 rho) > eps2 E, and tau >= 0.
+__global__ void combine_kernel(CombineArgs A)
+{
+    const int s = blockIdx.x;
+    const int E = A.edge[s], B = E + 2 * NG;
+    const long long FS = (long long)B * B * B;
+    const long long E3 = (long long)E * E * E;
+    const double dt = A.dt[0];
+    double a, b;
+    if (A.stage == 1) {
+        a = 0.0;
+        b = 1.0;
+    } else if (A.stage == 2) {
+        a = 0.75;
+        b = 0.25;
+    } else {
+        a = 1.0 / 3.0;
+        b = 2.0 / 3.0;
+    }
+    bool fired = false;
+    for (int c = threadIdx.x; c < E3; c += blockDim.x) {
+        int x = c % E, y = (c / E) % E, z = c / (E * E);
+        long long gi = A.off[s] + ((long long)(z + NG) * B + (y + NG)) * B + (x + NG);
+        long long li = A.doff[s] + c;
+        double u[MAXNF];
+#pragma unroll
+        for (int f = 0; f < MAXNF; f++) {
+            if (f < A.nf) {
+                double x1 = A.X[gi + f * FS] + dt * A.L[li + f * E3];
+                u[f] = (A.stage == 1) ? x1 : a * A.U0[gi + f * FS] + b * x1;
+            }
+        }
+        if (u[F_RHO] < A.rho_floor) {
+            u[F_RHO] = A.rho_floor;
+            fired = true;
+        }
+#pragma unroll
+        for (int f = F_SPC; f < MAXNF; f++)
+            if (f < A.nf && u[f] < 0.0) {
+                u[f] = 0.0;
+                fired = true;
+            }
+        double ei = u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) / u[F_RHO];
+        if (ei > A.eps2 * u[F_EGAS])
+            u[F_TAU] = pow(ei, 1.0 / A.gamma);
+        if (u[F_TAU] < 0.0) {
+            u[F_TAU] = 0.0;
+            fired = true;
+        }
+#pragma unroll
+        for (int f = 0; f < MAXNF; f++)
+            if (f < A.nf)
+                A.out[gi + f * FS] = u[f];
+    }
+    if (fired)
+        atomicOr(A.flags, 2u);
+}
+
+__device__ __forceinline__ int nb_slot(int dx, int dy, int dz)
+{
+    int n = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+    return n > 13 ? n - 1 : n;
+}
+
+// Ghost fill on a uniform level, one block per subgrid: each ghost cell
+// copies the matching interior cell of the neighbour subgrid; along an axis
+// whose face neighbour is missing (-1, a domain edge) the nearest interior
+// cell is copied instead (zero-gradient outflow).  Interiors are only read.
+__global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf, const int *nbr, unsigned *flags)
+{
+    const int s = blockIdx.x;
+    const int B = E + 2 * NG;
+    const long long FS = (long long)B * B * B;
+    const int *nb = nbr + 26 * (long long)s;
+    bool err = false;
+    for (int c = threadIdx.x; c < B * B * B; c += blockDim.x) {
+        int g[3] = {c % B - NG, (c / B) % B - NG, c / (B * B) - NG};
+        if (g[0] >= 0 && g[0] < E && g[1] >= 0 && g[1] < E && g[2] >= 0 && g[2] < E)
+            continue;
+        int d[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            d[a] = g[a] < 0 ? -1 : (g[a] >= E ? 1 : 0);
+            if (d[a] != 0) {
+                int dd[3] = {0, 0, 0};
+                dd[a] = d[a];
+                if (nb[nb_slot(dd[0], dd[1], dd[2])] < 0) {
+                    g[a] = d[a] < 0 ? 0 : E - 1;
+                    d[a] = 0;
+                }
+            }
+        }
+        int src = s;
+        if (d[0] || d[1] || d[2]) {
+            src = nb[nb_slot(d[0], d[1], d[2])];
+            if (src < 0) {
+                err = true;
+                continue;
+            }
+        }
+        long long si = off[src] + ((long long)(g[2] - d[2] * E + NG) * B + (g[1] - d[1] * E + NG)) * B +
+                       (g[0] - d[0] * E + NG);
+        long long di = off[s] + c;
+        for (int f = 0; f < nf; f++)
+            U[di + f * FS] = U[si + f * FS];
+    }
+    if (err)
+        atomicOr(flags, 4u);
+}
+
+}  // namespace octh

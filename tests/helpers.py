@@ -1,0 +1,48 @@
+"""Shared test helpers: device transfer of synthetic problems and the
+per-field error metric (max |gpu - oracle| over a field, divided by the
+field's max |oracle| over the batch)."""
+import numpy as np
+
+import oracle
+
+
+def field_errors(got, ref, nf, E3s):
+    """Per-field max relative error of two RHS-layout arrays."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    errs = []
+    idx = []
+    o = 0
+    for E3 in E3s:
+        idx.append((o, E3))
+        o += nf * E3
+    for f in range(nf):
+        g = np.concatenate([got[a + f * e: a + (f + 1) * e] for a, e in idx])
+        r = np.concatenate([ref[a + f * e: a + (f + 1) * e] for a, e in idx])
+        m = np.max(np.abs(r))
+        d = np.max(np.abs(g - r))
+        errs.append(0.0 if d == 0 else (d / m if m > 0 else np.inf))
+    return np.array(errs)
+
+
+def oracle_filled(prob):
+    """Copy of prob with ghosts filled by the oracle (when it has a table)."""
+    p = prob.copy()
+    if p.bc != 0:
+        oracle.ghost_fill(int(p.edge[0]), p.off, p.nf, p.nbr, p.U)
+    return p
+
+
+def e3s(prob):
+    return [int(E) ** 3 for E in prob.edge]
+
+
+def interior_layout(U, prob):
+    """Interior cells of a state array, in the RHS layout [s][f][E^3]."""
+    out = []
+    for s in range(prob.n_sub):
+        E = int(prob.edge[s])
+        B = E + 6
+        blk = U[prob.off[s]: prob.off[s] + prob.nf * B ** 3].reshape(prob.nf, B, B, B)
+        out.append(blk[:, 3:3 + E, 3:3 + E, 3:3 + E].reshape(-1))
+    return np.concatenate(out)

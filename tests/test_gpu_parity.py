@@ -1,0 +1,182 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Tolerances: FP64 form 1e-12 max relative error per field (error
+normalised by the field's max |oracle| over the batch); mixed form 1e-5;
+signal speeds and dt at the tolerance of a_q."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_06439_gb300 import inputs
+from tests.helpers import e3s, field_errors, interior_layout, oracle_filled
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _hydro(prob, precision=0, **kw):
+    from paper_2210_06439_gb300 import binding
+    return binding.Hydro.from_problem(prob, precision=precision, **kw)
+
+
+def _gpu_rhs(prob, precision=0, fill=True):
+    torch = _torch()
+    H = _hydro(prob, precision)
+    U = torch.from_numpy(prob.U).cuda()
+    if fill:
+        H.fill_ghosts(U)
+    d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+    am = torch.zeros(prob.n_sub, dtype=torch.float64, device="cuda")
+    H.rhs(U, d, am)
+    torch.cuda.synchronize()
+    flags = H.error_flags()
+    return d.cpu().numpy(), am.cpu().numpy(), flags, H, U
+
+
+def _check_rhs(prob, precision, tol=None):
+    ref = oracle_filled(prob)
+    d_o, am_o, nb = oracle.rhs(ref.edge, ref.off, ref.dx, ref.nf, ref.U, gamma=ref.gamma, nthreads=0)
+    assert nb == 0
+    d_g, am_g, flags, _, _ = _gpu_rhs(prob, precision)
+    assert flags == 0
+    errs = field_errors(d_g, d_o, prob.nf, e3s(prob))
+    tol = TOL[precision] if tol is None else tol
+    assert np.all(errs <= tol), errs
+    np.testing.assert_allclose(am_g, am_o, rtol=1e-12 if precision == 0 else 2e-6)
+    return errs
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sod_jump_single_subgrid(precision):
+    _check_rhs(inputs.sod_jump(), precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_periodic_box_2x2x2(precision):
+    _check_rhs(inputs.periodic_box(nsub=2), precision)
+
+
+@pytest.mark.parametrize("edge", [12, 16])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_periodic_box_larger_edges(edge, precision):
+    _check_rhs(inputs.periodic_box(nsub=2, E=edge), precision)
+
+
+def test_periodic_box_64_full_fp64():
+    _check_rhs(inputs.periodic_box(), 0)
+
+
+def test_uniform_state_exactly_zero_on_gpu():
+    for prec in (0, 1):
+        p = inputs.uniform_state(nsub=(2, 2, 1), v=(0.7, -0.4, 0.25))
+        d, am, flags, _, _ = _gpu_rhs(p, prec)
+        assert flags == 0
+        assert np.all(d == 0.0)
+
+
+def test_ghost_fill_bitwise():
+    torch = _torch()
+    for p in (inputs.periodic_box(nsub=2), inputs.binary_star(nsub=2)):
+        ref = oracle_filled(p)
+        H = _hydro(p)
+        U = torch.from_numpy(p.U).cuda()
+        H.fill_ghosts(U)
+        assert np.array_equal(U.cpu().numpy(), ref.U)
+
+
+def test_max_dt_matches_oracle():
+    p = inputs.periodic_box(nsub=2)
+    ref = oracle_filled(p)
+    _, am, _ = oracle.rhs(ref.edge, ref.off, ref.dx, ref.nf, ref.U)
+    dt_o = oracle.dt_from_amax(ref.dx, am, 0.4)
+    torch = _torch()
+    H = _hydro(p)
+    U = torch.from_numpy(ref.U).cuda()
+    dt_g = H.max_dt(U)
+    assert dt_g == pytest.approx(dt_o, rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rk3_step_periodic_matches_oracle_and_conserves(precision):
+    torch = _torch()
+    p = inputs.periodic_box(nsub=2)
+    ref = oracle_filled(p)
+    U0 = ref.U.copy()
+    dt_o, fired, st = oracle.rk3_step(ref.edge, ref.off, ref.dx, ref.nf, ref.U, bc=1, nbr=ref.nbr)
+    assert st == 0 and fired == 0
+    H = _hydro(p, precision)
+    U = torch.from_numpy(U0).cuda()
+    dt_g = H.rk_step(U)
+    assert H.error_flags() == 0
+    assert dt_g == pytest.approx(dt_o, rel=1e-12 if precision == 0 else 2e-6)
+    got = U.cpu().numpy()
+    gi, ri = interior_layout(got, p), interior_layout(ref.U, p)
+    errs = field_errors(gi, ri, p.nf, e3s(p))
+    assert np.all(errs <= (1e-12 if precision == 0 else 1e-6)), errs
+    # ghosts refreshed consistently with the interior
+    chk = p.copy()
+    chk.U[:] = got
+    oracle.ghost_fill(8, chk.off, chk.nf, chk.nbr, chk.U)
+    assert np.array_equal(chk.U, got)
+    # conservation of mass, momentum, energy
+    g1 = interior_layout(got, p).reshape(p.n_sub, p.nf, -1)
+    g0 = interior_layout(U0, p).reshape(p.n_sub, p.nf, -1)
+    lim = 1e-14 if precision == 0 else 1e-13
+    for f in range(5):
+        scale = math.fsum(np.abs(g0[:, f]).ravel())
+        assert abs(math.fsum(g1[:, f].ravel()) - math.fsum(g0[:, f].ravel())) <= lim * scale, f
+
+
+def test_rk3_graph_replay_is_deterministic():
+    torch = _torch()
+    p = oracle_filled(inputs.periodic_box(nsub=2))
+    H = _hydro(p)
+    outs = []
+    for _ in range(2):
+        U = torch.from_numpy(p.U).cuda()
+        for _ in range(3):
+            H.rk_step(U, want_dt=False)
+        torch.cuda.synchronize()
+        outs.append(U.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_mixed_levels_sampled_cells():
+    torch = _torch()
+    p = inputs.mixed_levels(n=96)
+    d_g, am_g, flags, _, _ = _gpu_rhs(p, 0, fill=False)
+    assert flags == 0
+    rng = np.random.default_rng(5)
+    smp = np.stack([rng.integers(0, p.n_sub, 200), np.zeros(200, np.int64)], axis=1)
+    smp[:, 1] = [rng.integers(0, int(p.edge[s]) ** 3) for s in smp[:, 0]]
+    ref = oracle.rhs_cells(p.edge, p.off, p.dx, p.nf, p.U, smp)
+    doff = np.concatenate([[0], np.cumsum(p.nf * p.edge.astype(np.int64) ** 3)])
+    for i, (s, c) in enumerate(smp):
+        E3 = int(p.edge[s]) ** 3
+        g = d_g[doff[s] + c + E3 * np.arange(p.nf)]
+        np.testing.assert_allclose(g, ref[i], rtol=1e-11, atol=1e-12 * np.max(np.abs(ref[i])))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_binary_star_small(precision):
+    _check_rhs(inputs.binary_star(nsub=4), precision)
+
+
+def test_nonphysical_input_sets_flag_without_trap():
+    torch = _torch()
+    p = oracle_filled(inputs.periodic_box(nsub=2))
+    p.block(3)[0, 7, 7, 7] = -1.0  # negative density in one interior cell
+    H = _hydro(p)
+    U = torch.from_numpy(p.U).cuda()
+    d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+    H.rhs(U, d)
+    torch.cuda.synchronize()
+    assert H.error_flags() & 1
+    assert H.error_flags() == 0  # read-and-clear
