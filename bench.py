@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched hydro RHS / SSP-RK3 step on GB300.
+
+One step = one full SSP-RK3 step (three RHS evaluations, the CFL dt
+reduction, three combines with floors and dual-energy re-synchronisation,
+three ghost fills) over the periodic 64^3 box of 512 subgrids of 8^3 cells
+with 5 species, in FP64, replayed from the library's CUDA graph.  Inputs are
+resident in HBM before the timed region; L2 is flushed (256 MiB write)
+between timed steps, each step timed by its own CUDA events on the launching
+stream.  The mixed form and the RHS alone are measured the same way and
+reported beside the headline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on the host cores for the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "hydro cell-updates/s (FP64 vs mixed) and % of HBM roofline on 1 GB300"
+UNIT = "cell-updates/s"
+WORKLOAD = ("periodic_box_64: 512 subgrids of 8^3 cells (64^3 periodic box), 3 ghost layers, 5 species "
+            "(11 fields), log-normal density, seed 1002; one step = one SSP-RK3 step "
+            "(3 RHS + dt + 3 combine/floor + 3 ghost fill)")
+
+# ---------------------------------------------------------------------------
+# Work and byte counts per cell (the method's arithmetic as the oracle writes
+# it, each +, -, *, /, sqrt, compare, min, max counted as one operation;
+# every PPM line of a needed cell once, both sides of every face point).
+# ---------------------------------------------------------------------------
+OPS_PPM = 68          # 3 MC slopes (14 each), 2 interface values (5 each), CW84 constraints (16)
+OPS_PRIM = 18         # v (3), kinetic energy (7), e_int + switch (3), p (2), c (3)
+OPS_KT_FIELD = 8      # two physical fluxes and the KT combination per field
+OPS_KT_POINT = 3 + 4  # signal speed (3) and the pressure terms (4)
+OPS_SIMPSON_FIELD = 11
+OPS_DIV_FIELD = 6
+
+
+def rhs_counts(E: int, nf: int):
+    """(FP64 ops, algorithmic HBM bytes) per interior cell of an edge-E
+    subgrid with nf fields for one RHS evaluation."""
+    cells = E ** 3
+    ring = 6 * E * E  # cells just outside each face
+    line_cells = cells * 13 + ring * 9  # each ring cell needs the 9 lines that cross its face
+    faces = 3 * (E + 1) * E * E
+    ops = (line_cells * nf * OPS_PPM
+           + faces * 9 * (2 * OPS_PRIM + OPS_KT_POINT + nf * OPS_KT_FIELD)
+           + faces * nf * OPS_SIMPSON_FIELD
+           + cells * nf * OPS_DIV_FIELD)
+    B = E + 6
+    bytes_ = (B ** 3 + E ** 3) * nf * 8
+    return ops / cells, bytes_ / cells
+
+
+def step_bytes(E: int, nf: int):
+    """Algorithmic HBM bytes per interior cell of one RK3 step in the launch
+    split used (3 RHS reads of the ghosted state + RHS writes, 3 combines,
+    3 ghost fills)."""
+    B = E + 6
+    cells = E ** 3
+    ghosts = B ** 3 - cells
+    rhs = 3 * (B ** 3 + cells) * nf * 8
+    comb = (3 * cells * nf * 8            # stage 1: read U, L; write W
+            + 2 * 4 * cells * nf * 8)     # stages 2, 3: read U0, X, L; write out
+    gfill = 3 * 2 * ghosts * nf * 8
+    return (rhs + comb + gfill) / cells
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2210_06439_gb300 import binding, inputs
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    prob = inputs.periodic_box(seed=1002)
+    nf, E, n_cells = prob.nf, 8, prob.n_cells
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+
+    def make(precision):
+        H = binding.Hydro.from_problem(prob, precision=precision)
+        U = torch.from_numpy(prob.U).cuda()
+        with torch.cuda.stream(stream):
+            H.fill_ghosts(U, stream=stream)
+        dU = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+        return H, U, dU
+
+    def timed(fn, k, w):
+        """Runs fn w times untimed, then k times each between its own events
+        (L2 flushed before each).  Returns per-iteration ms."""
+        for _ in range(w):
+            with torch.cuda.stream(stream):
+                fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in evs:
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                a.record(stream)
+                fn()
+                b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    results = {}
+    sampler = ClockSampler(dev)
+    for prec in (binding.OCT_FP64, binding.OCT_MIXED):
+        H, U, dU = make(prec)
+        H.autotune(U, stream=stream)
+        U0 = U.clone()
+        # full RK3 step (graph replay) -- the timed step
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if prec == binding.OCT_FP64:
+            sampler.start()
+        step_ms = timed(lambda: H.rk_step(U, want_dt=False, stream=stream), args.steps, args.warmup)
+        if prec == binding.OCT_FP64:
+            clocks = sampler.stop()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        # the RHS kernel alone (dominant kernel), same stream
+        U.copy_(U0)
+        rhs_ms = timed(lambda: H.rhs(U, dU, stream=stream), args.steps, args.warmup)
+        flags = H.error_flags()
+        results[prec] = dict(step_ms=step_ms, rhs_ms=rhs_ms, flags=flags, H=H, U=U)
+
+    # end to end through the host-buffer ABI call (pinned host state)
+    H64 = results[binding.OCT_FP64]["H"]
+    Uh = torch.from_numpy(prob.U.copy()).pin_memory()
+    H64.fill_ghosts(results[binding.OCT_FP64]["U"], stream=stream)
+    Uh.copy_(results[binding.OCT_FP64]["U"].cpu())
+    H64.rk_steps_host(Uh, 1, stream=stream)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(max(3, min(args.steps, 10))):
+        t0 = time.perf_counter()
+        H64.rk_steps_host(Uh, 1, stream=stream)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+
+    # reduce over ranks: max time
+    def mx(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    s64 = results[binding.OCT_FP64]
+    smx = results[binding.OCT_MIXED]
+    tot64 = mx(sum(s64["step_ms"]))
+    totmx = mx(sum(smx["step_ms"]))
+    rhs64 = mx(statistics.mean(s64["rhs_ms"]))
+    rhsmx = mx(statistics.mean(smx["rhs_ms"]))
+    e2e = mx(statistics.median(e2e_ms))
+    if rank != 0:
+        return None
+    K = args.steps
+    ms_step = tot64 / K
+    value = world * n_cells / (ms_step * 1e-3)
+    ops_cell, bytes_cell = rhs_counts(E, nf)
+    hbm_peak, hbm_src = _peaks()
+    rhs_tflops = ops_cell * n_cells / (rhs64 * 1e-3) / 1e12
+    rhs_gbs = bytes_cell * n_cells / (rhs64 * 1e-3) / 1e9
+    mx_tflops = ops_cell * n_cells / (rhsmx * 1e-3) / 1e12
+    mx_gbs = bytes_cell * n_cells / (rhsmx * 1e-3) / 1e9
+    state_bytes = prob.U.nbytes
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded noisy gas law, periodic 64^3 box)",
+        "config": {"workload": WORKLOAD, "subgrids": prob.n_sub, "edge": E, "ghost": 3, "n_species": 5,
+                   "interior_cells": n_cells, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MiB write) before each timed step"},
+        "rhs": {"value": world * n_cells / (rhs64 * 1e-3), "unit": "RHS cell-updates/s", "ms": rhs64},
+        "mixed": {"value": world * n_cells / (totmx / K * 1e-3), "unit": UNIT, "ms_per_step": totmx / K,
+                  "rhs_value": world * n_cells / (rhsmx * 1e-3), "rhs_ms": rhsmx,
+                  "speedup_vs_fp64_step": ms_step / (totmx / K), "speedup_vs_fp64_rhs": rhs64 / rhsmx,
+                  "rhs_roofline": {"bound": "alu", "achieved": mx_tflops, "peak": FP32_PEAK_TFLOPS,
+                                   "unit": "TFLOP/s", "frac": mx_tflops / FP32_PEAK_TFLOPS,
+                                   "hbm_gbs": mx_gbs, "hbm_frac": mx_gbs / hbm_peak}},
+        "roofline": {"bound": "alu", "achieved": rhs_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": rhs_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "rhs_kernel<double> (FP64 RHS)", "ops_per_cell": ops_cell,
+                     "peak_source": "nominal FP64 of GB300 (1.25 TFLOP/s); a DFMA loop measured 1.0",
+                     "hbm": {"achieved": rhs_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": rhs_gbs / hbm_peak,
+                             "bytes_per_cell": bytes_cell, "peak_source": hbm_src}},
+        "e2e": {"value": world * n_cells / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes + 8,
+                "how": "oct_hydro_rk_steps_host on pinned host state: H2D copy, RK3 step, D2H copy, per step"},
+        "gpu_launches": 10 * K,
+        "clocks": clocks,
+        "error_flags": {"fp64": s64["flags"], "mixed": smx["flags"]},
+    }
+    if args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sample_sub=8, reps=2)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# The oracle (CPU) as the reference arm and the CPU baseline
+# ---------------------------------------------------------------------------
+def _oracle_step_time(nsub):
+    import numpy as np
+    import oracle
+    from paper_2210_06439_gb300 import inputs
+    p = inputs.periodic_box(seed=1002, nsub=nsub)
+    oracle.ghost_fill(8, p.off, p.nf, p.nbr, p.U)
+    t0 = time.perf_counter()
+    dt, fired, st = oracle.rk3_step(p.edge, p.off, p.dx, p.nf, p.U, bc=1, nbr=p.nbr, nthreads=0)
+    t = time.perf_counter() - t0
+    return t, p.n_cells
+
+
+def cpu_baseline(sample_sub=4, reps=1):
+    import oracle
+    ts = []
+    cells = 0
+    for _ in range(reps):
+        t, cells = _oracle_step_time(sample_sub)
+        ts.append(t)
+    t = min(ts)
+    return {"value": cells / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"one SSP-RK3 step of the {sample_sub * 8}^3 periodic box ({sample_sub ** 3} subgrids of 8^3), "
+                      f"best of {reps}, FP64 C oracle (gcc -O2, OpenMP over subgrids)"}
+
+
+def run_reference(args):
+    import oracle
+    oracle.build_oracle()
+    nsub = 4
+    for _ in range(args.warmup):
+        _oracle_step_time(nsub)
+    ts = []
+    cells = 0
+    for _ in range(args.steps):
+        t, cells = _oracle_step_time(nsub)
+        ts.append(t)
+    ms = 1e3 * sum(ts) / len(ts)
+    value = cells / (ms * 1e-3)
+    cb = {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+          "sample": f"one SSP-RK3 step of a {nsub * 8}^3 periodic box ({nsub ** 3} subgrids) per step, same law"}
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_sample": cb["sample"]},
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build() if rank == 0 else None
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+    args.cpu_baseline = args.cpu_baseline and rank == 0 and world == 1
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
