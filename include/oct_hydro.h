@@ -163,6 +163,34 @@ oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_
  * kernel on U_sample and keeps the fastest for this layout and precision. */
 oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, void *cuda_stream);
 
+/* Allocation-free RHS + CFL dt (the paper has no counterpart: this is a
+ * calling convention of this library, not a step of the method).
+ * For callers that cannot call cudaMalloc on their hot path: host programs
+ * whose device memory is all handed out by their own pool allocator, and
+ * programs that must not take the implicit device-wide synchronisation that
+ * cudaMalloc/cudaFree can cause.  The call needs no handle and allocates
+ * nothing; its scratch (work list, per-item signal speeds, flag word) is one
+ * fixed device array of 475,392 bytes in the library, reserved on every GPU
+ * that loads it and held until the process exits.
+ *   n_subgrids : 1..4096 (larger batches fail with OCT_E_ARG);
+ *   edge, n_species, gamma, precision, cfl, de_switch1 : as for
+ *                oct_hydro_create / oct_hydro_set_params;
+ *   U          : device, packed ghosted blocks (block s at element
+ *                s * round_up(nf * (edge+6)^3, 4)), ghosts valid;
+ *   dx         : device, n_subgrids cell widths;
+ *   dUdt       : device output, RHS layout (n_subgrids * nf * edge^3);
+ *   dt         : device output, one double, cfl * min_s dx_s / a_max,s.
+ * Results equal oct_hydro_rhs and oct_hydro_max_dt of a handle with the same
+ * layout and parameters.  The first call on a device sets that device up
+ * (scratch address, line tables, kernel attributes) and should come before
+ * any stream capture.  Every call shares the scratch array, which keeps the
+ * last call's contents: calls that overlap on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller.  Device
+ * error flags of this call are not reported. */
+oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_species, double gamma, int precision, double cfl,
+                                    double de_switch1, const double *U, const double *dx, double *dUdt, double *dt,
+                                    void *cuda_stream);
+
 /* Reads and clears the device error flags (OCT_FLAG_*); synchronises. */
 oct_status oct_hydro_get_error_flags(oct_hydro_t h, uint32_t *flags);
 

@@ -39,6 +39,7 @@ SIGNATURES = {
     "oct_hydro_rk_steps_host": (_I, [_P, _P, _I, _P, _P]),
     "oct_hydro_rhs_host": (_I, [_P, _P, _P, _P]),
     "oct_hydro_autotune": (_I, [_P, _P, _P]),
+    "oct_hydro_rhs_dt_noalloc": (_I, [_I, _I, _I, _D, _I, _D, _D, _P, _P, _P, _P, _P]),
     "oct_hydro_get_error_flags": (_I, [_P, _P]),
     "oct_hydro_last_error": (ctypes.c_char_p, []),
     "oct_hydro_destroy": (None, [_P]),

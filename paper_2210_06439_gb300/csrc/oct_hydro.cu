@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -778,4 +779,187 @@ extern "C" void oct_hydro_destroy(oct_hydro_t h)
     dfree(h->d_flags);
     dfree(h->d_dt);
     delete h;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free RHS + dt entry point.
+//
+// For callers that cannot call cudaMalloc on their hot path: host programs
+// whose device memory is all handed out by their own pool allocator (a
+// cudaMalloc there fails or fragments the pool), and programs that must not
+// take the implicit device-wide synchronisation that cudaMalloc/cudaFree can
+// cause.  Everything the RHS and dt kernels need beyond the caller's inputs
+// and outputs lives in one file-scope device array of fixed size, reserved
+// when the library is loaded on a device and kept until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int NA_MAX_SUB = 4096;              // largest batch the static scratch holds
+constexpr int NA_MAX_ITEMS = 4 * NA_MAX_SUB;  // at most 4 work items per subgrid (edge 12 or 16)
+constexpr size_t NA_FLAGS = 0;
+constexpr size_t NA_EDGE = 256;
+constexpr size_t NA_OFF = NA_EDGE + sizeof(int) * NA_MAX_SUB;
+constexpr size_t NA_DOFF = NA_OFF + sizeof(long long) * NA_MAX_SUB;
+constexpr size_t NA_ITEMS = NA_DOFF + sizeof(long long) * NA_MAX_SUB;
+constexpr size_t NA_AMAX = NA_ITEMS + sizeof(WorkItem) * NA_MAX_ITEMS;
+constexpr size_t NA_BYTES = NA_AMAX + sizeof(double) * NA_MAX_ITEMS;  // 475,392 bytes
+static_assert(NA_ITEMS % 16 == 0 && NA_OFF % 8 == 0 && NA_AMAX % 8 == 0, "scratch sub-array alignment");
+}  // namespace
+
+// The static scratch: flag word, per-subgrid edge / state offset / RHS
+// offset, the work list and the per-item signal speeds.  In host code this
+// name is only a stand-in for the device array; its device address comes from
+// cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char *base = nullptr;  // device address of g_noalloc_scratch
+    int n_sm = 0;
+    int ctas[2] = {0, 0};
+};
+static NoallocDevice g_noalloc[64];
+static std::mutex g_noalloc_mutex;
+
+// Packed uniform layout and work list of a batch, written into the static
+// scratch: block s at s * round4(nf * (E+6)^3), RHS at s * nf * E^3, tiles as
+// in the handle's default work list.
+__global__ void noalloc_layout_kernel(int n_sub, int E, int nf, int *edge, long long *off, long long *doff,
+                                      WorkItem *items)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sub)
+        return;
+    long long B = E + 2 * NG;
+    long long len = (nf * B * B * B + 3) / 4 * 4;
+    edge[s] = E;
+    off[s] = s * len;
+    doff[s] = (long long)s * nf * E * E * E;
+    int t = (E == 12) ? 6 : 8;
+    int per_row = E / t;
+    for (int k = 0; k < per_row * per_row; k++) {
+        WorkItem w;
+        w.s = s;
+        w.x0 = (k % per_row) * t;
+        w.y0 = (k / per_row) * t;
+        w.txty = t | (t << 8);
+        items[s * per_row * per_row + k] = w;
+    }
+}
+
+// Once per device, with that device current: the scratch address, the line
+// tables and the RHS kernels' launch attributes.
+static oct_status noalloc_setup(int dev, NoallocDevice **out)
+{
+    if (dev < 0 || dev >= 64)
+        return fail(OCT_E_CUDA, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoallocDevice &d = g_noalloc[dev];
+    if (!d.ready) {
+        void *p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        oct_status st = ensure_tables(dev);
+        if (st != OCT_OK)
+            return st;
+        CUDA_TRY(cudaDeviceGetAttribute(&d.n_sm, cudaDevAttrMultiProcessorCount, dev));
+        oct_hydro tmp;  // only its nf feeds the shared-memory plan
+        for (int prec = 0; prec < 2; prec++) {
+            tmp.nf = MAXNF;
+            size_t sm = rhs_smem(&tmp, prec);
+            const void *fn =
+                prec == OCT_FP64 ? (const void *)rhs_kernel<double, false> : (const void *)rhs_kernel<float, true>;
+            CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            int nb = 0;
+            CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NTHREADS, sm));
+            if (nb < 1)
+                return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM");
+            d.ctas[prec] = nb;
+        }
+        d.base = (unsigned char *)p;
+        d.ready = true;
+    }
+    *out = &d;
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_species, double gamma, int precision,
+                                               double cfl, double de_switch1, const double *U, const double *dx,
+                                               double *dUdt, double *dt, void *cuda_stream)
+{
+    if (n_subgrids <= 0 || n_subgrids > NA_MAX_SUB)
+        return fail(OCT_E_ARG,
+                    "n_subgrids must be in 1..%d, the size of the static scratch of the allocation-free call "
+                    "(got %d)",
+                    NA_MAX_SUB, n_subgrids);
+    if (!valid_edge(edge))
+        return fail(OCT_E_ARG, "edge must be 8, 12 or 16 (got %d)", edge);
+    if (n_species < 0 || n_species > MAXNF - 6)
+        return fail(OCT_E_ARG, "n_species must be in 0..%d (got %d)", MAXNF - 6, n_species);
+    if (!(gamma > 1.0) || !std::isfinite(gamma))
+        return fail(OCT_E_ARG, "gamma must be > 1 (got %g)", gamma);
+    if (precision != OCT_FP64 && precision != OCT_MIXED)
+        return fail(OCT_E_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+    if (!(cfl > 0.0 && cfl <= 1.0))
+        return fail(OCT_E_ARG, "cfl must be in (0, 1] (got %g)", cfl);
+    if (!(de_switch1 >= 0.0 && de_switch1 < 1.0))
+        return fail(OCT_E_ARG, "de_switch1 must be in [0, 1)");
+    oct_status st;
+    if ((st = check_ptr(U, "U")) != OCT_OK || (st = check_ptr(dUdt, "dUdt")) != OCT_OK)
+        return st;
+    if (!dx || !dt)
+        return fail(OCT_E_ARG, "dx and dt must not be NULL");
+    const int nf = 6 + n_species;
+    const long long B = edge + 2 * NG;
+    const long long state_len = (long long)n_subgrids * ((nf * B * B * B + 3) / 4 * 4);
+    const long long rhs_len = (long long)n_subgrids * nf * edge * edge * edge;
+    const char *u0 = (const char *)U, *u1 = u0 + state_len * 8;
+    const char *d0 = (const char *)dUdt, *d1 = d0 + rhs_len * 8;
+    if (u0 < d1 && d0 < u1)
+        return fail(OCT_E_ARG, "U and dUdt overlap");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    NoallocDevice *D = nullptr;
+    if ((st = noalloc_setup(dev, &D)) != OCT_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned char *base = D->base;
+    const int per = (edge == 8) ? 1 : 4;
+    const int n_items = n_subgrids * per;
+    unsigned *flags = (unsigned *)(base + NA_FLAGS);
+    int *d_edge = (int *)(base + NA_EDGE);
+    long long *d_off = (long long *)(base + NA_OFF);
+    long long *d_doff = (long long *)(base + NA_DOFF);
+    WorkItem *d_items = (WorkItem *)(base + NA_ITEMS);
+    double *d_amax = (double *)(base + NA_AMAX);
+    // the flag word is the only part that has to start at zero; every other
+    // entry is rewritten below before it is read
+    CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(unsigned), s));
+    noalloc_layout_kernel<<<(n_subgrids + 127) / 128, 128, 0, s>>>(n_subgrids, edge, nf, d_edge, d_off, d_doff,
+                                                                     d_items);
+    CUDA_TRY(cudaGetLastError());
+    RhsArgs A;
+    A.U = U;
+    A.dUdt = dUdt;
+    A.amax_tile = d_amax;
+    A.edge = d_edge;
+    A.off = d_off;
+    A.doff = d_doff;
+    A.dx = dx;
+    A.items = d_items;
+    A.n_items = n_items;
+    A.nf = nf;
+    A.gamma = gamma;
+    A.eps1 = de_switch1;
+    A.flags = flags;
+    oct_hydro tmp;
+    tmp.nf = nf;
+    size_t sm = rhs_smem(&tmp, precision);
+    int grid = std::min(n_items, D->n_sm * D->ctas[precision]);
+    if (precision == OCT_FP64)
+        rhs_kernel<double, false><<<grid, NTHREADS, sm, s>>>(A);
+    else
+        rhs_kernel<float, true><<<grid, NTHREADS, sm, s>>>(A);
+    CUDA_TRY(cudaGetLastError());
+    dt_kernel<<<1, 1024, 0, s>>>(n_items, d_items, dx, d_amax, cfl, 0.0, dt);
+    CUDA_TRY(cudaGetLastError());
+    return OCT_OK;
 }
