@@ -133,8 +133,8 @@ struct oct_hydro {
     std::vector<WorkItem> items;
     std::vector<int> item_begin;
     long long state_len = 0, rhs_len = 0;
-    int tile_mode = 0;       // 0: 8x8 (6x6 for edge 12); 1: 8x4 split
-    int ctas_per_sm[2] = {0, 0};
+    int tile_mode = 0;       // 0: 8x8 tiles (6x6 for edge 12); 1: 8x4 tiles (6x4 for edge 12)
+    int ctas_per_sm[2][2] = {{0, 0}, {0, 0}};  // [precision][tile mode]
     // device memory
     int *d_edge = nullptr, *d_nbr = nullptr, *d_item_begin = nullptr;
     long long *d_off = nullptr, *d_doff = nullptr;
@@ -195,23 +195,47 @@ static void free_layout(oct_hydro *h)
     drop_graphs(h);
 }
 
-static size_t rhs_smem(const oct_hydro *h, int prec)
+// RHS kernel instances: tile capacity 8x8 (one CTA per SM) or 8x4 (two).
+static size_t rhs_smem_of(int nf, int prec, int mode)
 {
-    return smem_plan(h->nf, prec == OCT_FP64 ? 8 : 4, prec != OCT_FP64).total;
+    return smem_plan(nf, prec == OCT_FP64 ? 8 : 4, prec != OCT_FP64, 8, mode == 0 ? 8 : 4).total;
+}
+
+static const void *rhs_fn(int prec, int mode)
+{
+    if (prec == OCT_FP64)
+        return mode == 0 ? (const void *)rhs_kernel<double, false, 8, 8, 1> : (const void *)rhs_kernel<double, false, 8, 4, 2>;
+    return mode == 0 ? (const void *)rhs_kernel<float, true, 8, 8, 1> : (const void *)rhs_kernel<float, true, 8, 4, 2>;
+}
+
+static void rhs_launch(int prec, int mode, int grid, size_t sm, cudaStream_t st, const RhsArgs &A)
+{
+    if (prec == OCT_FP64) {
+        if (mode == 0)
+            rhs_kernel<double, false, 8, 8, 1><<<grid, NTHREADS, sm, st>>>(A);
+        else
+            rhs_kernel<double, false, 8, 4, 2><<<grid, NTHREADS, sm, st>>>(A);
+    } else {
+        if (mode == 0)
+            rhs_kernel<float, true, 8, 8, 1><<<grid, NTHREADS, sm, st>>>(A);
+        else
+            rhs_kernel<float, true, 8, 4, 2><<<grid, NTHREADS, sm, st>>>(A);
+    }
 }
 
 static oct_status set_kernel_attrs(oct_hydro *h)
 {
-    for (int prec = 0; prec < 2; prec++) {
-        size_t sm = rhs_smem(h, prec);
-        const void *fn = prec == OCT_FP64 ? (const void *)rhs_kernel<double, false> : (const void *)rhs_kernel<float, true>;
-        CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        int nb = 0;
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NTHREADS, sm));
-        if (nb < 1)
-            return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM (%zu bytes shared memory)", sm);
-        h->ctas_per_sm[prec] = nb;
-    }
+    for (int prec = 0; prec < 2; prec++)
+        for (int mode = 0; mode < 2; mode++) {
+            size_t sm = rhs_smem_of(h->nf, prec, mode);
+            const void *fn = rhs_fn(prec, mode);
+            CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            int nb = 0;
+            CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NTHREADS, sm));
+            if (nb < 1)
+                return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM (%zu bytes shared memory)", sm);
+            h->ctas_per_sm[prec][mode] = nb;
+        }
     return OCT_OK;
 }
 
@@ -222,14 +246,8 @@ static void build_items(oct_hydro *h)
     for (int s = 0; s < h->n_sub; s++) {
         h->item_begin[s] = (int)h->items.size();
         int E = h->edge[s];
-        int tx, ty;
-        if (E == 12) {
-            tx = ty = 6;
-        } else {
-            tx = ty = 8;
-            if (h->tile_mode == 1)
-                ty = 4;
-        }
+        int tx = (E == 12) ? 6 : 8;
+        int ty = (h->tile_mode == 1) ? 4 : tx;
         for (int y0 = 0; y0 < E; y0 += ty)
             for (int x0 = 0; x0 < E; x0 += tx) {
                 WorkItem w;
@@ -490,13 +508,9 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
     A.gamma = h->gamma;
     A.eps1 = h->eps1;
     A.flags = h->d_flags;
-    int prec = h->precision;
-    int grid = std::min<int>(A.n_items, h->n_sm * h->ctas_per_sm[prec]);
-    size_t sm = rhs_smem(h, prec);
-    if (prec == OCT_FP64)
-        rhs_kernel<double, false><<<grid, NTHREADS, sm, st>>>(A);
-    else
-        rhs_kernel<float, true><<<grid, NTHREADS, sm, st>>>(A);
+    const int prec = h->precision, mode = h->tile_mode;
+    int grid = std::min<int>(A.n_items, h->n_sm * h->ctas_per_sm[prec][mode]);
+    rhs_launch(prec, mode, grid, rhs_smem_of(h->nf, prec, mode), st, A);
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;
 }
@@ -861,12 +875,9 @@ static oct_status noalloc_setup(int dev, NoallocDevice **out)
         if (st != OCT_OK)
             return st;
         CUDA_TRY(cudaDeviceGetAttribute(&d.n_sm, cudaDevAttrMultiProcessorCount, dev));
-        oct_hydro tmp;  // only its nf feeds the shared-memory plan
         for (int prec = 0; prec < 2; prec++) {
-            tmp.nf = MAXNF;
-            size_t sm = rhs_smem(&tmp, prec);
-            const void *fn =
-                prec == OCT_FP64 ? (const void *)rhs_kernel<double, false> : (const void *)rhs_kernel<float, true>;
+            size_t sm = rhs_smem_of(MAXNF, prec, 0);
+            const void *fn = rhs_fn(prec, 0);
             CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             int nb = 0;
             CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NTHREADS, sm));
@@ -950,14 +961,9 @@ extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_s
     A.gamma = gamma;
     A.eps1 = de_switch1;
     A.flags = flags;
-    oct_hydro tmp;
-    tmp.nf = nf;
-    size_t sm = rhs_smem(&tmp, precision);
+    size_t sm = rhs_smem_of(nf, precision, 0);
     int grid = std::min(n_items, D->n_sm * D->ctas[precision]);
-    if (precision == OCT_FP64)
-        rhs_kernel<double, false><<<grid, NTHREADS, sm, s>>>(A);
-    else
-        rhs_kernel<float, true><<<grid, NTHREADS, sm, s>>>(A);
+    rhs_launch(precision, 0, grid, sm, s, A);
     CUDA_TRY(cudaGetLastError());
     dt_kernel<<<1, 1024, 0, s>>>(n_items, d_items, dx, d_amax, cfl, 0.0, dt);
     CUDA_TRY(cudaGetLastError());

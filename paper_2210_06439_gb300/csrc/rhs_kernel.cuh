@@ -36,77 +36,288 @@ template <class T> struct Num;
 template <> struct Num<double> {
     __device__ static __forceinline__ double from_d(double x) { return x; }
     __device__ static __forceinline__ double to_d(double x) { return x; }
-    __device__ static __forceinline__ double sqrt_(double x) { return sqrt(x); }
     __device__ static __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 };
 template <> struct Num<float> {
     __device__ static __forceinline__ float from_d(double x) { return d2f_rn(x); }
     __device__ static __forceinline__ double to_d(float x) { return f2d(x); }
-    __device__ static __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     __device__ static __forceinline__ float pow_(float x, float y) { return powf(x, y); }
 };
 
-// Monotonised-central slope: minmod of the centred and twice the one-sided
-// differences, zero unless all three share a strict sign.
-template <class T>
-__device__ __forceinline__ T mc_slope(T um, T u0, T up)
+// ---------------------------------------------------------------------------
+// FP64 helpers that keep work off the FP64 pipe.  GB300 retires FP64
+// arithmetic, compares, min/max and f64<->f32 conversions at about 1/64 of
+// the FP32 rate, so sign tests, magnitude comparisons and power-of-two
+// scalings are done on the bit patterns with integer operations (valid for
+// normal numbers; the rare zero/subnormal/huge operands take a plain FP64
+// path), and reciprocals and square roots start from an FP32 estimate and
+// are refined by Newton-Raphson steps in FP64.
+// ---------------------------------------------------------------------------
+constexpr long long ABSM = 0x7FFFFFFFFFFFFFFFLL;
+constexpr long long SGNM = (long long)0x8000000000000000ULL;
+constexpr long long EXP1 = 1LL << 52;
+
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(long long b) { return __longlong_as_double(b); }
+
+// double -> float for operands known to be in the normal float range,
+// truncating the mantissa (an estimate only); returns false otherwise.
+__device__ __forceinline__ bool d2f_est(double x, float &f)
 {
-    T c = T(0.5) * (up - um);
-    T l = T(2) * (u0 - um);
-    T r = T(2) * (up - u0);
-    T mag = fmin(fabs(c), fmin(fabs(l), fabs(r)));
-    bool pos = (c > T(0)) && (l > T(0)) && (r > T(0));
-    bool neg = (c < T(0)) && (l < T(0)) && (r < T(0));
-    return pos ? mag : (neg ? -mag : T(0));
+    long long b = dbits(x);
+    int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+    unsigned int m = (unsigned int)((b >> 29) & 0x7FFFFF);
+    f = __uint_as_float(((unsigned int)(b >> 32) & 0x80000000u) | ((unsigned int)e << 23) | m);
+    return e > 1 && e < 253;
 }
 
-// CW84 PPM on u_{-2..2}: limited values at the cell's two ends.
+__device__ __forceinline__ double f2d_normal(float f)
+{
+    unsigned int b = __float_as_uint(f);
+    unsigned long long e = ((b >> 23) & 0xFF) - 127 + 1023;
+    return bitsd((long long)(((unsigned long long)(b & 0x80000000u) << 32) | (e << 52) |
+                             ((unsigned long long)(b & 0x7FFFFF) << 29)));
+}
+
+// 1/x: FP32 reciprocal estimate (rcp.approx, about 2^-22 relative), then two
+// Newton-Raphson steps r <- r + r (1 - x r), each squaring the relative error.
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    float xf;
+    if (!d2f_est(x, xf))
+        return 1.0 / x;
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+    double r = f2d_normal(rf);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
+// sqrt(q): FP32 reciprocal-square-root estimate y (about 2^-22), s = q y,
+// then two Newton (Heron) corrections s <- s + (q - s^2) y / 2.
+__device__ __forceinline__ double sqrt_nr(double q)
+{
+    float qf;
+    if (!d2f_est(q, qf))
+        return sqrt(q);
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(qf));
+    double y = f2d_normal(yf);
+    double h = f2d_normal(0.5f * yf);
+    double s = q * y;
+    double r = fma(-s, s, q);
+    s = fma(r, h, s);
+    r = fma(-s, s, q);
+    return fma(r, h, s);
+}
+
+// The sign, zero and magnitude tests below work on the two 32-bit halves of
+// a double: written on the 64-bit pattern they would be recognised and issued
+// as FP64 compares and min/max, which is what they are meant to avoid.
+struct HL {
+    int h;           // high word (sign, exponent, top 20 mantissa bits)
+    unsigned int l;  // low word
+};
+__device__ __forceinline__ HL hl(double x) { return HL{__double2hiint(x), (unsigned int)__double2loint(x)}; }
+__device__ __forceinline__ double from_hl(int h, unsigned int l) { return __hiloint2double(h, (int)l); }
+// |x| as (high word without sign, low word)
+__device__ __forceinline__ bool is_zero(HL a) { return ((a.h & 0x7FFFFFFF) | a.l) == 0u; }
+// |a| < |b| for the magnitude words (high words already without sign)
+__device__ __forceinline__ bool mag_lt(int ah, unsigned int al, int bh, unsigned int bl)
+{
+    return ((unsigned int)ah < (unsigned int)bh) || (ah == bh && al < bl);
+}
+
+// max of two non-negative (or NaN) doubles by their bit patterns
+__device__ __forceinline__ double max_nonneg(double x, double y)
+{
+    const HL X = hl(x), Y = hl(y);
+    return mag_lt(X.h, X.l, Y.h, Y.l) ? y : x;
+}
+__device__ __forceinline__ float max_nonneg(float x, float y) { return fmaxf(x, y); }
+
+// Monotonised-central slope from the two one-sided differences a = u0 - u-1
+// and b = u1 - u0: minmod((a + b)/2, 2a, 2b), zero unless a and b share a
+// strict sign.
+__device__ __forceinline__ double mc_slope(double a, double b)
+{
+    const HL A = hl(a), Bv = hl(b);
+    const bool same = ((A.h ^ Bv.h) >= 0) && !is_zero(A) && !is_zero(Bv);
+    if (!same)
+        return 0.0;
+    const double s = a + b;
+    const HL S = hl(s);
+    const int ah = A.h & 0x7FFFFFFF, bh = Bv.h & 0x7FFFFFFF, sh = S.h & 0x7FFFFFFF;
+    // m = min(|a|, |b|)
+    const bool alb = mag_lt(ah, A.l, bh, Bv.l);
+    const int mh = alb ? ah : bh;
+    const unsigned int ml = alb ? A.l : Bv.l;
+    const int em = mh >> 20, es = sh >> 20;
+    int rh;
+    unsigned int rl;
+    if (em >= 1 && em <= 2043 && es >= 2 && es <= 2046) {
+        // |s|/2 <= 2 m  <=>  |s| <= 4 m: compare with m's exponent raised by 2
+        if (!mag_lt(mh + (2 << 20), ml, sh, S.l)) {
+            rh = sh - (1 << 20);  // |s| / 2
+            rl = S.l;
+        } else {
+            rh = mh + (1 << 20);  // 2 m
+            rl = ml;
+        }
+    } else {
+        const HL R = hl(fmin(0.5 * fabs(s), 2.0 * from_hl(mh, ml)));
+        rh = R.h;
+        rl = R.l;
+    }
+    return from_hl(rh | (A.h & (int)0x80000000), rl);
+}
+__device__ __forceinline__ float mc_slope(float a, float b)
+{
+    float s = a + b;
+    float m = fminf(fabsf(a), fabsf(b));
+    float r = fminf(0.5f * fabsf(s), 2.0f * m);
+    bool same = (a > 0.f && b > 0.f) || (a < 0.f && b < 0.f);
+    return same ? copysignf(r, a) : 0.f;
+}
+
+// CW84 monotonicity constraints on (um, u0, up) written with d1 = up - u0,
+// d2 = u0 - um: flat at an extremum (d1 d2 <= 0); otherwise the parabola
+// overshoots on the minus side exactly when |d2| > 2|d1| (then um = u0 - 2 d1)
+// and on the plus side when |d1| > 2|d2| (then up = u0 + 2 d2).
+__device__ __forceinline__ void cw84_limit(double u0, double &um, double &up)
+{
+    const double d1 = up - u0, d2 = u0 - um;
+    const HL D1 = hl(d1), D2 = hl(d2);
+    if (((D1.h ^ D2.h) < 0) || is_zero(D1) || is_zero(D2)) {
+        um = u0;
+        up = u0;
+        return;
+    }
+    const int h1 = D1.h & 0x7FFFFFFF, h2 = D2.h & 0x7FFFFFFF;
+    const int e1 = h1 >> 20, e2 = h2 >> 20;
+    bool A, Bp;
+    if (e1 >= 1 && e1 <= 2045 && e2 >= 1 && e2 <= 2045) {
+        A = mag_lt(h1 + (1 << 20), D1.l, h2, D2.l);   // |d2| > 2|d1|
+        Bp = mag_lt(h2 + (1 << 20), D2.l, h1, D1.l);  // |d1| > 2|d2|
+    } else {
+        A = fabs(d2) > 2.0 * fabs(d1);
+        Bp = fabs(d1) > 2.0 * fabs(d2);
+    }
+    if (A)
+        um = fma(-2.0, d1, u0);
+    else if (Bp)
+        up = fma(2.0, d2, u0);
+}
+__device__ __forceinline__ void cw84_limit(float u0, float &um, float &up)
+{
+    float d1 = up - u0, d2 = u0 - um;
+    if (d1 * d2 <= 0.f) {
+        um = u0;
+        up = u0;
+        return;
+    }
+    if (fabsf(d2) > 2.f * fabsf(d1))
+        um = fmaf(-2.f, d1, u0);
+    else if (fabsf(d1) > 2.f * fabsf(d2))
+        up = fmaf(2.f, d2, u0);
+}
+
+// CW84 PPM on u_{-2..2}: limited values at the cell's two ends.  The
+// interface value (u0 + u1)/2 - (du1 - du0)/6 is formed as
+// u0 + (u1 - u0)/2 + (du0 - du1)/6.
 template <class T>
 __device__ __forceinline__ void ppm5(T um2, T um1, T u0, T up1, T up2, T &vm, T &vp)
 {
-    T dm = mc_slope(um2, um1, u0);
-    T d0 = mc_slope(um1, u0, up1);
-    T dp = mc_slope(u0, up1, up2);
-    T up = T(0.5) * (u0 + up1) - (dp - d0) * T(1.0 / 6.0);
-    T um = T(0.5) * (um1 + u0) - (d0 - dm) * T(1.0 / 6.0);
-    T a = up - u0, b = u0 - um;
-    if (a * b <= T(0)) {
-        um = u0;
-        up = u0;
-    } else {
-        T du = up - um;
-        T m6 = du * (u0 - T(0.5) * (up + um));
-        T dd = du * du * T(1.0 / 6.0);
-        if (m6 > dd)
-            um = T(3) * u0 - T(2) * up;
-        else if (-dd > m6)
-            up = T(3) * u0 - T(2) * um;
-    }
+    const T am2 = um1 - um2, am1 = u0 - um1, ap1 = up1 - u0, ap2 = up2 - up1;
+    const T dm = mc_slope(am2, am1);
+    const T d0 = mc_slope(am1, ap1);
+    const T dp = mc_slope(ap1, ap2);
+    const T s6 = T(1.0 / 6.0);
+    T up = fma(d0 - dp, s6, fma(T(0.5), ap1, u0));
+    T um = fma(d0 - dm, -s6, fma(T(-0.5), am1, u0));
+    cw84_limit(u0, um, up);
     vm = um;
     vp = up;
 }
 
-// Shared-memory plan of one CTA (dynamic shared memory), sizes for the
-// largest tile (8 x 8) and nf fields.
+// Point primitives: velocity, pressure (dual energy) and sound speed.
+__device__ __forceinline__ void prim_point(const double *q, double gamma, double gm1, double ggm1, double eps1,
+                                           double *v, double &p, double &c, bool &bad)
+{
+    const double rho = q[F_RHO];
+    const double ir = rcp_nr(rho);
+    const double vx = q[F_SX] * ir, vy = q[F_SY] * ir, vz = q[F_SZ] * ir;
+    const double sv = fma(q[F_SZ], vz, fma(q[F_SY], vy, q[F_SX] * vx));
+    double ei = fma(-0.5, sv, q[F_EGAS]);
+    double c2;
+    if (ei < eps1 * q[F_EGAS]) {
+        ei = pow(q[F_TAU], gamma);
+        p = gm1 * ei;
+        c2 = gamma * p * ir;
+    } else {
+        p = gm1 * ei;
+        c2 = ggm1 * ei * ir;
+    }
+    // c2 > 0 (and finite) on the high word; zero gives c = 0; a negative or
+    // non-finite c2 or rho is reported as non-physical
+    const int ch = __double2hiint(c2), rh = __double2hiint(rho);
+    c = (ch > 0 && ch < 0x7FF00000) ? sqrt_nr(c2) : (is_zero(hl(c2)) ? 0.0 : sqrt(c2));
+    v[0] = vx;
+    v[1] = vy;
+    v[2] = vz;
+    bad |= !(rh > 0 && rh < 0x7FF00000) || !(ch >= 0 && ch < 0x7FF00000);
+}
+__device__ __forceinline__ void prim_point(const float *q, float gamma, float gm1, float ggm1, float eps1,
+                                           float *v, float &p, float &c, bool &bad)
+{
+    const float rho = q[F_RHO];
+    const float ir = __fdividef(1.f, rho);
+    const float vx = q[F_SX] * ir, vy = q[F_SY] * ir, vz = q[F_SZ] * ir;
+    const float sv = fmaf(q[F_SZ], vz, fmaf(q[F_SY], vy, q[F_SX] * vx));
+    float ei = fmaf(-0.5f, sv, q[F_EGAS]);
+    float c2;
+    if (ei < eps1 * q[F_EGAS]) {
+        ei = powf(q[F_TAU], gamma);
+        p = gm1 * ei;
+        c2 = gamma * p * ir;
+    } else {
+        p = gm1 * ei;
+        c2 = ggm1 * ei * ir;
+    }
+    c = c2 > 0.f ? c2 * rsqrtf(c2) : sqrtf(c2);
+    v[0] = vx;
+    v[1] = vy;
+    v[2] = vz;
+    bad |= !(rho > 0.f) || !(c == c);
+}
+
+// Shared-memory plan of one CTA (dynamic shared memory) for a tile capacity
+// of txm x tym cells and nf fields.
 struct SmemPlan {
-    int nc;          // cells per plane buffer row: 64 interior + 32 ring
-    size_t temp, saved, faccx, faccy, zacc, dxy, raw, red, total;
+    int nc;          // cells per plane buffer row: interior + ring
+    size_t temp, saved, pr, prs, faccx, faccy, zacc, dxy, raw, red, lists, total;
 };
 
-__host__ __device__ inline SmemPlan smem_plan(int nf, int elem, bool staged)
+__host__ __device__ inline SmemPlan smem_plan(int nf, int elem, bool staged, int txm, int tym)
 {
     SmemPlan p;
-    p.nc = MAXT * MAXT + 4 * MAXT;
+    const int cin = txm * tym;
+    p.nc = cin + 2 * txm + 2 * tym;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o += (bytes + 15) / 16 * 16; return at; };
     p.temp = take((size_t)8 * nf * p.nc * elem);
-    p.saved = take((size_t)9 * nf * MAXT * MAXT * elem);
-    p.faccx = take((size_t)nf * (MAXT + 1) * MAXT * elem);
-    p.faccy = take((size_t)nf * (MAXT + 1) * MAXT * elem);
-    p.zacc = take((size_t)2 * nf * MAXT * MAXT * elem);
-    p.dxy = take((size_t)nf * MAXT * MAXT * sizeof(double));
-    p.raw = staged ? take((size_t)5 * nf * (MAXT + 2 * NG) * (MAXT + 2 * NG) * sizeof(float)) : 0;
+    p.saved = take((size_t)9 * nf * cin * elem);
+    p.pr = take((size_t)8 * 5 * p.nc * elem);
+    p.prs = take((size_t)9 * 5 * cin * elem);
+    p.faccx = take((size_t)nf * (txm + 1) * tym * elem);
+    p.faccy = take((size_t)nf * txm * (tym + 1) * elem);
+    p.zacc = take((size_t)2 * nf * cin * elem);
+    p.dxy = take((size_t)nf * cin * sizeof(double));
+    p.raw = staged ? take((size_t)5 * nf * (tym + 2 * NG) * (txm + 2 * NG) * sizeof(float)) : 0;
     p.red = take(64 * sizeof(double));
+    p.lists = take((size_t)4 * p.nc * sizeof(int));
     p.total = o;
     return p;
 }
@@ -126,82 +337,35 @@ __device__ __forceinline__ int cidx(int i, int j, int tx, int ty)
     return tx * ty + 2 * ty + tx + i;
 }
 
-// Point primitives and flux at one quadrature point.  qL, qR: point values of
-// the nf fields on both sides; k: face normal; w: Simpson weight.  Adds
-// w * F_KT to acc and returns the local signal speed a.
-template <class T>
-__device__ __forceinline__ T kt_point(int k, int nf, const T *qL, const T *qR, T w, T gamma, T eps1, T *acc,
-                                      bool &bad)
-{
-    T vL[3], vR[3], pL, pR, cL, cR;
-    {
-        T rho = qL[F_RHO], ir = T(1) / rho;
-        vL[0] = qL[F_SX] * ir;
-        vL[1] = qL[F_SY] * ir;
-        vL[2] = qL[F_SZ] * ir;
-        T ek = T(0.5) * (qL[F_SX] * vL[0] + qL[F_SY] * vL[1] + qL[F_SZ] * vL[2]);
-        T ei = qL[F_EGAS] - ek;
-        if (ei < eps1 * qL[F_EGAS])
-            ei = Num<T>::pow_(qL[F_TAU], gamma);
-        pL = (gamma - T(1)) * ei;
-        cL = Num<T>::sqrt_(gamma * pL * ir);
-        bad |= !(rho > T(0)) || !(cL == cL);
-    }
-    {
-        T rho = qR[F_RHO], ir = T(1) / rho;
-        vR[0] = qR[F_SX] * ir;
-        vR[1] = qR[F_SY] * ir;
-        vR[2] = qR[F_SZ] * ir;
-        T ek = T(0.5) * (qR[F_SX] * vR[0] + qR[F_SY] * vR[1] + qR[F_SZ] * vR[2]);
-        T ei = qR[F_EGAS] - ek;
-        if (ei < eps1 * qR[F_EGAS])
-            ei = Num<T>::pow_(qR[F_TAU], gamma);
-        pR = (gamma - T(1)) * ei;
-        cR = Num<T>::sqrt_(gamma * pR * ir);
-        bad |= !(rho > T(0)) || !(cR == cR);
-    }
-    const T vkL = k == 0 ? vL[0] : (k == 1 ? vL[1] : vL[2]);
-    const T vkR = k == 0 ? vR[0] : (k == 1 ? vR[1] : vR[2]);
-    T a = fmax(fabs(vkL) + cL, fabs(vkR) + cR);
-    // F_f = (F_f(L) + F_f(R))/2 - a (u_R - u_L)/2, written per side:
-    // alpha u_L + beta u_R with alpha = (v_L + a)/2, beta = (v_R - a)/2,
-    // plus the pressure terms of the normal momentum and the energy.
-    T al = T(0.5) * (vkL + a) * w;
-    T be = T(0.5) * (vkR - a) * w;
-    const T pm = T(0.5) * w * (pL + pR);
-    const T pe = T(0.5) * w * (pL * vkL + pR * vkR);
-#pragma unroll
-    for (int f = 0; f < MAXNF; f++)
-        if (f < nf) {
-            T add = al * qL[f] + be * qR[f];
-            if (f == F_SX + k)
-                add += pm;
-            if (f == F_EGAS)
-                add += pe;
-            acc[f] += add;
-        }
-    return a;
-}
-
-template <class T, bool STAGED>
-__global__ void __launch_bounds__(NTHREADS, 1) rhs_kernel(RhsArgs A)
+template <class T, bool STAGED, int TXM, int TYM, int MINB>
+__global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int nf = A.nf;
-    const SmemPlan P = smem_plan(nf, sizeof(T), STAGED);
-    const int NC = P.nc;
-    T *temp = reinterpret_cast<T *>(smem + P.temp);    // [8 slots][nf][NC]
-    T *saved = reinterpret_cast<T *>(smem + P.saved);  // [9][nf][64]
+    const SmemPlan P = smem_plan(nf, sizeof(T), STAGED, TXM, TYM);
+    constexpr int NC = TXM * TYM + 2 * TXM + 2 * TYM;
+    constexpr int C64 = TXM * TYM;                 // interior cells of a full tile
+    constexpr int FXS = (TXM + 1) * TYM;           // x faces of a full tile
+    constexpr int FYS = TXM * (TYM + 1);           // y faces
+    constexpr int XW = (FXS + 31) / 32 * 32, YW = (FYS + 31) / 32 * 32, ZW = (C64 + 31) / 32 * 32;
+    static_assert(XW + YW + ZW <= NTHREADS, "face threads exceed the block");
+    T *temp = reinterpret_cast<T *>(smem + P.temp);    // [8 slots][nf][NC] point values of the group
+    T *saved = reinterpret_cast<T *>(smem + P.saved);  // [9][nf][64] +z ends of the previous plane
+    T *pr = reinterpret_cast<T *>(smem + P.pr);        // [8 slots][5][NC] vx, vy, vz, p, c of the group
+    T *prs = reinterpret_cast<T *>(smem + P.prs);      // [9][5][64] the same for the saved +z ends
     T *faccx = reinterpret_cast<T *>(smem + P.faccx);  // [nf][72]
     T *faccy = reinterpret_cast<T *>(smem + P.faccy);  // [nf][72]
     T *zacc = reinterpret_cast<T *>(smem + P.zacc);    // [2][nf][64]
     double *dxy = reinterpret_cast<double *>(smem + P.dxy);  // [nf][64]
     float *raw = reinterpret_cast<float *>(smem + P.raw);    // [5][nf][14][14]
     double *red = reinterpret_cast<double *>(smem + P.red);
+    int *lists = reinterpret_cast<int *>(smem + P.lists);    // [4][96] packed cells
     const int tid = threadIdx.x;
     const T gamma = Num<T>::from_d(A.gamma);
+    const T gm1 = Num<T>::from_d(A.gamma - 1.0);
+    const T ggm1 = Num<T>::from_d(A.gamma * (A.gamma - 1.0));
     const T eps1 = Num<T>::from_d(A.eps1);
-    const int RW = MAXT + 2 * NG;  // staged row width
+    constexpr int RWX = TXM + 2 * NG, RWY = TYM + 2 * NG;  // staged plane shape
     bool bad = false;
 
     for (int it = blockIdx.x; it < A.n_items; it += gridDim.x) {
@@ -215,36 +379,58 @@ __global__ void __launch_bounds__(NTHREADS, 1) rhs_kernel(RhsArgs A)
         const int ncin = tx * ty;
         double amax = 0.0;
 
-        // raw field value at tile-relative (i, j) of plane kz (interior coords)
-        auto rawv = [&](int f, int kz, int j, int i) -> T {
-            if constexpr (STAGED) {
-                int slot = (kz + 3 + 10) % 5;
-                return (T)raw[((slot * nf + f) * RW + (j + NG)) * RW + (i + NG)];
-            } else {
-                return Num<T>::from_d(__ldg(Ub + f * FS + (long long)(kz + NG) * B * B + (long long)(y0 + j + NG) * B +
-                                            (x0 + i + NG)));
-            }
-        };
         auto stage_plane = [&](int kz) {
             if constexpr (STAGED) {
-                int slot = (kz + 3 + 10) % 5;
+                int slot = (kz + 3) % 5;
                 int rows = ty + 2 * NG, cols = tx + 2 * NG;
                 int n = nf * rows * cols;
                 for (int q = tid; q < n; q += NTHREADS) {
-                    int f = q / (rows * cols), r = q % (rows * cols);
-                    int jj = r / cols, ii = r % cols;
+                    int f = q / (rows * cols), r = q - f * (rows * cols);
+                    int jj = r / cols, ii = r - jj * cols;
                     double v = __ldg(Ub + f * FS + (long long)(kz + NG) * B * B + (long long)(y0 + jj) * B + (x0 + ii));
-                    raw[((slot * nf + f) * RW + jj) * RW + ii] = d2f_rn(v);
+                    raw[((slot * nf + f) * RWY + jj) * RWX + ii] = d2f_rn(v);
                 }
             }
         };
-
-        // zero accumulators
-        for (int q = tid; q < nf * (MAXT + 1) * MAXT; q += NTHREADS) {
-            faccx[q] = T(0);
-            faccy[q] = T(0);
+        // cell lists of a plane: 0 interior, 1 + x ring, 2 + y ring, 3 both;
+        // entry = (i + 1) | (j + 1) << 8 | compact index << 16
+        int nlist[4];
+        nlist[0] = ncin;
+        nlist[1] = ncin + 2 * ty;
+        nlist[2] = ncin + 2 * tx;
+        nlist[3] = ncin + 2 * tx + 2 * ty;
+        for (int q = tid; q < 4 * NC; q += NTHREADS) {
+            int t = q / NC, c = q % NC;
+            if (c >= nlist[t])
+                continue;
+            int i, j;
+            if (c < ncin) {
+                i = c % tx;
+                j = c / tx;
+            } else {
+                int r = c - ncin;
+                if ((t & 1) && r < 2 * ty) {
+                    i = (r < ty) ? -1 : tx;
+                    j = r % ty;
+                } else {
+                    if (t & 1)
+                        r -= 2 * ty;
+                    j = (r < tx) ? -1 : ty;
+                    i = r % tx;
+                }
+            }
+            lists[q] = (i + 1) | ((j + 1) << 8) | (cidx(i, j, tx, ty) << 16);
         }
-        for (int q = tid; q < 2 * nf * MAXT * MAXT; q += NTHREADS)
+        unsigned magic[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+            magic[t] = (unsigned)((0x100000000ULL + nlist[t] - 1) / nlist[t]);
+
+        for (int q = tid; q < nf * FXS; q += NTHREADS)
+            faccx[q] = T(0);
+        for (int q = tid; q < nf * FYS; q += NTHREADS)
+            faccy[q] = T(0);
+        for (int q = tid; q < 2 * nf * C64; q += NTHREADS)
             zacc[q] = T(0);
         for (int kz = -3; kz <= 1; kz++)
             stage_plane(kz);
@@ -252,152 +438,255 @@ __global__ void __launch_bounds__(NTHREADS, 1) rhs_kernel(RhsArgs A)
 
         for (int kz = -1; kz <= E; kz++) {
             const bool inplane = (kz >= 0 && kz < E);
+            int so[5];  // staged-ring offsets of planes kz-2 .. kz+2
+#pragma unroll
+            for (int m = 0; m < 5; m++)
+                so[m] = ((kz + m + 1) % 5) * nf * RWY * RWX;
             for (int g = 0; g < NGROUPS; g++) {
                 const GroupTab &G = c_groups[g];
                 if (!inplane && !G.has[2])
                     continue;
-                // ---- phase A: 1-D PPM for every (line, field, cell) ----
-                int ncl[4], tot = 0;
-                for (int l = 0; l < G.nl; l++) {
-                    int n = ncin;
-                    if (inplane) {
-                        if (G.line[l][0]) n += 2 * ty;
-                        if (G.line[l][1]) n += 2 * tx;
-                    }
-                    ncl[l] = n;
-                    tot += nf * n;
-                }
-                for (int q = tid; q < tot; q += NTHREADS) {
-                    int r = q, l = 0;
-                    while (r >= nf * ncl[l]) {
-                        r -= nf * ncl[l];
-                        l++;
-                    }
-                    int f = r / ncl[l], c = r % ncl[l];
-                    const int ddx = G.line[l][0], ddy = G.line[l][1], ddz = G.line[l][2];
-                    int i, j;
-                    if (c < ncin) {
-                        i = c % tx;
-                        j = c / tx;
-                    } else {
-                        c -= ncin;
-                        if (ddx && c < 2 * ty) {
-                            i = (c < ty) ? -1 : tx;
-                            j = c % ty;
-                        } else {
-                            if (ddx) c -= 2 * ty;
-                            j = (c < tx) ? -1 : ty;
-                            i = c % tx;
+                const int nl = G.nl;
+                // cells of each line's list: the x / y ring only for lines with
+                // a nonzero x / y step, and only in planes that own x / y faces
+                auto ltype = [&](int l) -> int {
+                    return inplane ? ((G.line[l][0] != 0) | ((G.line[l][1] != 0) << 1)) : 0;
+                };
+                const int t0 = ltype(0), t1 = nl > 1 ? ltype(1) : 0, t2 = nl > 2 ? ltype(2) : 0,
+                          t3 = nl > 3 ? ltype(3) : 0;
+                const int n0 = nlist[t0], n1 = nl > 1 ? nlist[t1] : 0, n2 = nl > 2 ? nlist[t2] : 0,
+                          n3 = nl > 3 ? nlist[t3] : 0;
+                const int totA = (n0 + n1 + n2 + n3) * nf;
+                // ---- phase A: 1-D PPM for every (line, field, cell) of the group ----
+                for (int q = tid; q < totA; q += NTHREADS) {
+                    int l = 0, r = q, t = t0, n = n0;
+                    if (r >= n0 * nf) {
+                        r -= n0 * nf;
+                        l = 1, t = t1, n = n1;
+                        if (r >= n1 * nf) {
+                            r -= n1 * nf;
+                            l = 2, t = t2, n = n2;
+                            if (r >= n2 * nf) {
+                                r -= n2 * nf;
+                                l = 3, t = t3, n = n3;
+                            }
                         }
                     }
+                    const unsigned mg = t == 0 ? magic[0] : (t == 1 ? magic[1] : (t == 2 ? magic[2] : magic[3]));
+                    const int f = __umulhi((unsigned)r, mg);
+                    const int c = r - f * n;
+                    const int info = lists[t * NC + c];
+                    const int i = (info & 0xFF) - 1, j = ((info >> 8) & 0xFF) - 1, ci = info >> 16;
+                    const int ddx = G.line[l][0], ddy = G.line[l][1], ddz = G.line[l][2];
                     T u[5];
+                    if constexpr (STAGED) {
+                        const float *rb = raw + f * RWY * RWX + (j + NG) * RWX + (i + NG);
+                        const int step = ddy * RWX + ddx;
 #pragma unroll
-                    for (int m = -2; m <= 2; m++)
-                        u[m + 2] = rawv(f, kz + m * ddz, j + m * ddy, i + m * ddx);
+                        for (int m = -2; m <= 2; m++) {
+                            const int pz = ddz > 0 ? so[m + 2] : (ddz < 0 ? so[2 - m] : so[2]);
+                            u[m + 2] = (T)rb[pz + m * step];
+                        }
+                    } else {
+                        const long long st = (long long)ddz * B * B + (long long)ddy * B + ddx;
+                        const double *ub = Ub + f * FS + (long long)(kz + NG) * B * B + (long long)(y0 + j + NG) * B +
+                                           (x0 + i + NG);
+#pragma unroll
+                        for (int m = -2; m <= 2; m++)
+                            u[m + 2] = Num<T>::from_d(__ldg(ub + m * st));
+                    }
                     T vm, vp;
-                    ppm5(u[0], u[1], u[2], u[3], u[4], vm, vp);
-                    int ci = cidx(i, j, tx, ty);
-                    temp[((2 * l + 0) * nf + f) * NC + ci] = vm;
+                    ppm5<T>(u[0], u[1], u[2], u[3], u[4], vm, vp);
+                    temp[((2 * l) * nf + f) * NC + ci] = vm;
                     temp[((2 * l + 1) * nf + f) * NC + ci] = vp;
                 }
                 __syncthreads();
-                // ---- phase B: one thread per face ----
-                const int nfx = (inplane && G.has[0]) ? (tx + 1) * ty : 0;
-                const int nfy = (inplane && G.has[1]) ? tx * (ty + 1) : 0;
-                const int nfz = G.has[2] ? ncin : 0;
-                for (int q = tid; q < nfx + nfy + nfz; q += NTHREADS) {
-                    T acc[MAXNF];
+                // ---- phase B1: primitives of every needed point of the group ----
+                {
+                    const int tot = 2 * (n0 + n1 + n2 + n3);
+                    for (int q = tid; q < tot; q += NTHREADS) {
+                        int l = 0, r = q, t = t0, n = n0;
+                        if (r >= 2 * n0) {
+                            r -= 2 * n0;
+                            l = 1, t = t1, n = n1;
+                            if (r >= 2 * n1) {
+                                r -= 2 * n1;
+                                l = 2, t = t2, n = n2;
+                                if (r >= 2 * n2) {
+                                    r -= 2 * n2;
+                                    l = 3, t = t3, n = n3;
+                                }
+                            }
+                        }
+                        const int e = r >= n;
+                        const int c = r - e * n;
+                        const int info = lists[t * NC + c];
+                        const int i = (info & 0xFF) - 1, j = ((info >> 8) & 0xFF) - 1, ci = info >> 16;
+                        const int sg = e ? 1 : -1;  // direction of this end = sg * line
+                        const int ex = sg * G.line[l][0], ey = sg * G.line[l][1], ez = sg * G.line[l][2];
+                        bool need;
+                        if (!inplane)
+                            need = (kz < 0) ? (ez == 1) : (ez == -1);
+                        else if (i < 0)
+                            need = ex == 1;
+                        else if (i >= tx)
+                            need = ex == -1;
+                        else if (j < 0)
+                            need = ey == 1;
+                        else if (j >= ty)
+                            need = ey == -1;
+                        else
+                            need = true;
+                        if (!need)
+                            continue;
+                        const int slot = 2 * l + e;
+                        T qh[6];
 #pragma unroll
-                    for (int f = 0; f < MAXNF; f++)
-                        acc[f] = T(0);
-                    T qL[MAXNF], qR[MAXNF];
-                    int axis, cl, cr, fslot;
-                    if (q < nfx) {
+                        for (int f = 0; f < 6; f++)
+                            qh[f] = temp[(slot * nf + f) * NC + ci];
+                        T v[3], p, cs;
+                        prim_point(qh, gamma, gm1, ggm1, eps1, v, p, cs, bad);
+                        T *o = pr + slot * 5 * NC + ci;
+                        o[0] = v[0];
+                        o[NC] = v[1];
+                        o[2 * NC] = v[2];
+                        o[3 * NC] = p;
+                        o[4 * NC] = cs;
+                    }
+                }
+                __syncthreads();
+                // ---- phase B2: KT flux at the group's points, one thread per face;
+                // warp-aligned ranges of threads for x, y and z faces ----
+                {
+                    int axis, cl = 0, cr = 0, fslot = 0;
+                    bool act;
+                    if (tid < XW) {
                         axis = 0;
-                        int p = q % (tx + 1), j = q / (tx + 1);
-                        cl = cidx(p - 1, j, tx, ty);
-                        cr = cidx(p, j, tx, ty);
-                        fslot = q;
-                    } else if (q < nfx + nfy) {
+                        act = inplane && G.has[0] && tid < (tx + 1) * ty;
+                        if (act) {
+                            int p = tid % (tx + 1), j = tid / (tx + 1);
+                            cl = cidx(p - 1, j, tx, ty);
+                            cr = cidx(p, j, tx, ty);
+                            fslot = tid;
+                        }
+                    } else if (tid < XW + YW) {
                         axis = 1;
-                        int r = q - nfx;
-                        int i = r % tx, p = r / tx;
-                        cl = cidx(i, p - 1, tx, ty);
-                        cr = cidx(i, p, tx, ty);
-                        fslot = r;
+                        int r = tid - XW;
+                        act = inplane && G.has[1] && r < tx * (ty + 1);
+                        if (act) {
+                            int i = r % tx, p = r / tx;
+                            cl = cidx(i, p - 1, tx, ty);
+                            cr = cidx(i, p, tx, ty);
+                            fslot = r;
+                        }
                     } else {
                         axis = 2;
-                        cl = cr = fslot = q - nfx - nfy;
+                        int r = tid - XW - YW;
+                        act = G.has[2] && r < ncin;
+                        cl = cr = fslot = r;
                     }
-                    if (axis < 2 || kz >= 0) {
+                    if (act && (axis < 2 || kz >= 0)) {
+                        T acc[MAXNF];
+#pragma unroll
+                        for (int f = 0; f < MAXNF; f++)
+                            acc[f] = T(0);
                         for (int pt = 0; pt < G.npt; pt++) {
                             if (G.axis[pt] != axis)
                                 continue;
                             const T w = G.wcls[pt] == 0 ? T(16.0 / 36.0) : (G.wcls[pt] == 1 ? T(4.0 / 36.0) : T(1.0 / 36.0));
-                            int ls = G.lslot[pt], rs = G.rslot[pt];
-#pragma unroll
-                            for (int f = 0; f < MAXNF; f++) {
-                                if (f < nf) {
-                                    qL[f] = (ls >= 16) ? saved[((ls - 16) * nf + f) * (MAXT * MAXT) + cl]
-                                                       : temp[(ls * nf + f) * NC + cl];
-                                    qR[f] = temp[(rs * nf + f) * NC + cr];
-                                }
+                            const int ls = G.lslot[pt], rs = G.rslot[pt];
+                            const T *qL, *pL_;
+                            int sL;
+                            if (ls >= 16) {
+                                qL = saved + (ls - 16) * nf * C64 + cl;
+                                pL_ = prs + (ls - 16) * 5 * C64 + cl;
+                                sL = C64;
+                            } else {
+                                qL = temp + ls * nf * NC + cl;
+                                pL_ = pr + ls * 5 * NC + cl;
+                                sL = NC;
                             }
-                            T a = kt_point<T>(axis, nf, qL, qR, w, gamma, eps1, acc, bad);
-                            amax = fmax(amax, (double)Num<T>::to_d(a));
+                            const T *qR = temp + rs * nf * NC + cr;
+                            const T *pR_ = pr + rs * 5 * NC + cr;
+                            const T vkL = pL_[axis * sL], pLv = pL_[3 * sL], cL = pL_[4 * sL];
+                            const T vkR = pR_[axis * NC], pRv = pR_[3 * NC], cR = pR_[4 * NC];
+                            const T a = max_nonneg(fabs(vkL) + cL, fabs(vkR) + cR);
+                            amax = max_nonneg(amax, Num<T>::to_d(a));
+                            // F_f = (F_f(L) + F_f(R))/2 - a (u_R - u_L)/2 written per side:
+                            // alpha u_L + beta u_R, alpha = (v_L + a)/2, beta = (v_R - a)/2,
+                            // plus the pressure terms of the normal momentum and the energy
+                            const T hw = T(0.5) * w;
+                            const T al = (vkL + a) * hw;
+                            const T be = (vkR - a) * hw;
+#pragma unroll
+                            for (int f = 0; f < MAXNF; f++)
+                                if (f < nf)
+                                    acc[f] = fma(al, qL[f * sL], fma(be, qR[f * NC], acc[f]));
+                            const T pm = (pLv + pRv) * hw;
+                            const T pe = fma(pLv, vkL, pRv * vkR) * hw;
+#pragma unroll
+                            for (int k = 0; k < 3; k++)
+                                if (k == axis)
+                                    acc[F_SX + k] += pm;
+                            acc[F_EGAS] += pe;
                         }
-                        T *dst = axis == 0 ? faccx : (axis == 1 ? faccy : zacc + (kz & 1) * nf * MAXT * MAXT);
-                        const int stride = axis == 2 ? MAXT * MAXT : (MAXT + 1) * MAXT;
+                        T *dst = axis == 0 ? faccx : (axis == 1 ? faccy : zacc + (kz & 1) * nf * C64);
+                        const int stride = axis == 2 ? C64 : (axis == 0 ? FXS : FYS);
 #pragma unroll
                         for (int f = 0; f < MAXNF; f++)
                             if (f < nf)
                                 dst[f * stride + fslot] += acc[f];
                     }
-                    if (axis == 2 && kz < E) {
-                        // leave this plane's +z ends for the z faces of the next plane
-                        for (int z = 0; z < G.nzp; z++)
+                    if (axis == 2 && act && kz < E) {
+                        // leave this plane's +z ends (values and primitives) for the next plane
+                        for (int z = 0; z < G.nzp; z++) {
+                            const int src = G.zp_src[z], dsts = G.zp_dst[z];
                             for (int f = 0; f < nf; f++)
-                                saved[(G.zp_dst[z] * nf + f) * (MAXT * MAXT) + cl] =
-                                    temp[(G.zp_src[z] * nf + f) * NC + cl];
+                                saved[(dsts * nf + f) * C64 + cl] = temp[(src * nf + f) * NC + cl];
+#pragma unroll
+                            for (int v = 0; v < 5; v++)
+                                prs[(dsts * 5 + v) * C64 + cl] = pr[(src * 5 + v) * NC + cl];
+                        }
                     }
                 }
                 __syncthreads();
             }
             // ---- finish the divergence of plane kz-1 (its upper z face is done) ----
             if (kz >= 1) {
-                const T *zp = zacc + (kz & 1) * nf * MAXT * MAXT;
-                const T *zm = zacc + ((kz - 1) & 1) * nf * MAXT * MAXT;
+                const T *zp = zacc + (kz & 1) * nf * C64;
+                const T *zm = zacc + ((kz - 1) & 1) * nf * C64;
                 for (int q = tid; q < nf * ncin; q += NTHREADS) {
-                    int f = q / ncin, c = q % ncin;
+                    int f = q / ncin, c = q - f * ncin;
                     int i = c % tx, j = c / tx;
-                    double dz = Num<T>::to_d(zp[f * MAXT * MAXT + c]) - Num<T>::to_d(zm[f * MAXT * MAXT + c]);
-                    double d = -(dxy[f * MAXT * MAXT + c] + dz) * rdx;
+                    double dz = Num<T>::to_d(zp[f * C64 + c]) - Num<T>::to_d(zm[f * C64 + c]);
+                    double d = -(dxy[f * C64 + c] + dz) * rdx;
                     dUb[(long long)f * E * E * E + (long long)(kz - 1) * E * E + (long long)(y0 + j) * E + (x0 + i)] = d;
                 }
             }
             __syncthreads();
             if (kz >= 1) {
-                T *zm = zacc + ((kz - 1) & 1) * nf * MAXT * MAXT;
-                for (int q = tid; q < nf * MAXT * MAXT; q += NTHREADS)
+                T *zm = zacc + ((kz - 1) & 1) * nf * C64;
+                for (int q = tid; q < nf * C64; q += NTHREADS)
                     zm[q] = T(0);
             }
             if (inplane) {
                 for (int q = tid; q < nf * ncin; q += NTHREADS) {
-                    int f = q / ncin, c = q % ncin;
+                    int f = q / ncin, c = q - f * ncin;
                     int i = c % tx, j = c / tx;
-                    const T *fx = faccx + f * (MAXT + 1) * MAXT;
-                    const T *fy = faccy + f * (MAXT + 1) * MAXT;
+                    const T *fx = faccx + f * FXS;
+                    const T *fy = faccy + f * FYS;
                     double dX = Num<T>::to_d(fx[j * (tx + 1) + i + 1]) - Num<T>::to_d(fx[j * (tx + 1) + i]);
                     double dY = Num<T>::to_d(fy[(j + 1) * tx + i]) - Num<T>::to_d(fy[j * tx + i]);
-                    dxy[f * MAXT * MAXT + c] = dX + dY;
+                    dxy[f * C64 + c] = dX + dY;
                 }
             }
             __syncthreads();
-            if (inplane)
-                for (int q = tid; q < nf * (MAXT + 1) * MAXT; q += NTHREADS) {
+            if (inplane) {
+                for (int q = tid; q < nf * FXS; q += NTHREADS)
                     faccx[q] = T(0);
+                for (int q = tid; q < nf * FYS; q += NTHREADS)
                     faccy[q] = T(0);
-                }
+            }
             if (kz + 3 <= E + 2)
                 stage_plane(kz + 3);
             __syncthreads();

@@ -1,6 +1,6 @@
 """Runs the RHS kernel a few times on one workload, for profiling under ncu.
 
-  python -m paper_2210_06439_gb300.profile_rhs --precision 0 --nsub 8 --reps 3
+  python -m paper_2210_06439_gb300.profile_rhs --precision 0 --nsub 8 --reps 3 [--autotune]
 
 precision 0 = FP64, 1 = mixed; the workload is the periodic box of nsub^3
 subgrids of 8^3 cells with 5 species (ghosts filled on the device)."""
@@ -17,11 +17,14 @@ def main():
     ap.add_argument("--nsub", type=int, default=8)
     ap.add_argument("--edge", type=int, default=8)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--autotune", action="store_true", help="run the autotuner first (8 trial launches)")
     a = ap.parse_args()
     p = inputs.periodic_box(nsub=a.nsub, E=a.edge)
     H = binding.Hydro.from_problem(p, precision=a.precision)
     U = torch.from_numpy(p.U).cuda()
     H.fill_ghosts(U)
+    if a.autotune:
+        H.autotune(U)
     d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
     for _ in range(a.reps):
         H.rhs(U, d)
