@@ -32,20 +32,32 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "hydro cell-updates/s (FP64 vs mixed) and % of HBM roofline on 1 GB300"
+WORKLOADS = {
+    # name: (description, generator of the full workload, generator of the oracle's CPU sample)
+    "periodic_box_64": ("512 subgrids of 8^3 cells (64^3 periodic box), 3 ghost layers, 5 species (11 fields), "
+                        "log-normal density, seed 1002", lambda inp: inp.periodic_box(seed=1002),
+                        lambda inp: inp.periodic_box(seed=1002)),
+    "mixed_levels": ("4096 subgrids of edge 8/12/16 on 3 levels (dx halving), ghosts given, 5 species, seed 1003",
+                     lambda inp: inp.mixed_levels(), lambda inp: inp.mixed_levels(n=96)),
+    "binary_star_128": ("4096 subgrids of 8^3 (128^3 outflow box), two n=1.5 polytropes (mass ratio 0.7) in a "
+                        "1e-10 atmosphere, Keplerian rotation, 5 species", lambda inp: inp.binary_star(16),
+                        lambda inp: inp.binary_star(4)),
+    "binary_star_256": ("32768 subgrids of 8^3 (256^3 outflow box), the binary-star law, 5 species",
+                        lambda inp: inp.binary_star(32), lambda inp: inp.binary_star(4)),
+}
 UNIT = "cell-updates/s"
-WORKLOAD = ("periodic_box_64: 512 subgrids of 8^3 cells (64^3 periodic box), 3 ghost layers, 5 species "
-            "(11 fields), log-normal density, seed 1002; one step = one SSP-RK3 step "
-            "(3 RHS + dt + 3 combine/floor + 3 ghost fill)")
+STEP = "one step = one SSP-RK3 step (3 RHS + dt + 3 combine/floor + 3 ghost fill), FP64"
 
 # ---------------------------------------------------------------------------
-# Work and byte counts per cell (the method's arithmetic as the oracle writes
-# it, each +, -, *, /, sqrt, compare, min, max counted as one operation;
-# every PPM line of a needed cell once, both sides of every face point).
+# Work and byte counts per cell: the floating-point arithmetic of the
+# method's formulas as the oracle writes them (+, -, *, /, sqrt; compares,
+# min and max are not counted), every PPM line of a needed cell once, both
+# sides' primitives at every face point.
 # ---------------------------------------------------------------------------
-OPS_PPM = 68          # 3 MC slopes (14 each), 2 interface values (5 each), CW84 constraints (16)
-OPS_PRIM = 18         # v (3), kinetic energy (7), e_int + switch (3), p (2), c (3)
+OPS_PPM = 38          # 3 MC slopes (6 each), 2 interface values (5 each), CW84 constraint terms (10)
+OPS_PRIM = 17         # v (3), kinetic energy (7), e_int and its switch (2), p (2), c^2 and sqrt (3)
 OPS_KT_FIELD = 8      # two physical fluxes and the KT combination per field
-OPS_KT_POINT = 3 + 4  # signal speed (3) and the pressure terms (4)
+OPS_KT_POINT = 2 + 4  # signal speeds (2) and the pressure terms (4)
 OPS_SIMPSON_FIELD = 11
 OPS_DIV_FIELD = 6
 
@@ -64,6 +76,16 @@ def rhs_counts(E: int, nf: int):
     B = E + 6
     bytes_ = (B ** 3 + E ** 3) * nf * 8
     return ops / cells, bytes_ / cells
+
+
+def problem_counts(prob):
+    """(FP64 ops, algorithmic bytes) per interior cell of one RHS over a batch."""
+    ops = byt = 0.0
+    for E in prob.edge:
+        o, b = rhs_counts(int(E), prob.nf)
+        ops += o * int(E) ** 3
+        byt += b * int(E) ** 3
+    return ops / prob.n_cells, byt / prob.n_cells
 
 
 def step_bytes(E: int, nf: int):
@@ -91,6 +113,22 @@ def _peaks():
 
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def reduce_max(v: float, world: int, device="cuda") -> float:
+    """Max of a per-rank scalar over all ranks (identity on one rank)."""
+    if world == 1:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(cells_per_rank: int, world: int, ms_total_max: float, steps: int):
+    """Whole-job throughput: every rank's cells over the slowest rank's time."""
+    ms_step = ms_total_max / steps
+    return world * cells_per_rank / (ms_step * 1e-3), ms_step
 
 
 # ---------------------------------------------------------------------------
@@ -157,8 +195,8 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    prob = inputs.periodic_box(seed=1002)
-    nf, E, n_cells = prob.nf, 8, prob.n_cells
+    prob = WORKLOADS[args.workload][1](inputs)
+    nf, n_cells = prob.nf, prob.n_cells
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
 
     def make(precision):
@@ -208,7 +246,8 @@ def run_ours(args, rank, world):
         U.copy_(U0)
         rhs_ms = timed(lambda: H.rhs(U, dU, stream=stream), args.steps, args.warmup)
         flags = H.error_flags()
-        results[prec] = dict(step_ms=step_ms, rhs_ms=rhs_ms, flags=flags, H=H, U=U)
+        results[prec] = dict(step_ms=step_ms, rhs_ms=rhs_ms, flags=flags, H=H, U=U, dU=dU, U0=U0,
+                             tile_mode=H.tile_mode())
 
     # end to end through the host-buffer ABI call (pinned host state)
     H64 = results[binding.OCT_FP64]["H"]
@@ -224,26 +263,21 @@ def run_ours(args, rank, world):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
 
     # reduce over ranks: max time
-    def mx(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
     s64 = results[binding.OCT_FP64]
     smx = results[binding.OCT_MIXED]
-    tot64 = mx(sum(s64["step_ms"]))
-    totmx = mx(sum(smx["step_ms"]))
-    rhs64 = mx(statistics.mean(s64["rhs_ms"]))
-    rhsmx = mx(statistics.mean(smx["rhs_ms"]))
-    e2e = mx(statistics.median(e2e_ms))
+    tot64 = reduce_max(sum(s64["step_ms"]), world)
+    totmx = reduce_max(sum(smx["step_ms"]), world)
+    rhs64 = reduce_max(statistics.mean(s64["rhs_ms"]), world)
+    rhsmx = reduce_max(statistics.mean(smx["rhs_ms"]), world)
+    e2e = reduce_max(statistics.median(e2e_ms), world)
+    mixed_err = None
+    if args.cpu_baseline and rank == 0 and prob.n_cells <= 2 ** 21:
+        mixed_err = mixed_error_table(prob, results, stream)
     if rank != 0:
         return None
     K = args.steps
-    ms_step = tot64 / K
-    value = world * n_cells / (ms_step * 1e-3)
-    ops_cell, bytes_cell = rhs_counts(E, nf)
+    value, ms_step = aggregate(n_cells, world, tot64, K)
+    ops_cell, bytes_cell = problem_counts(prob)
     hbm_peak, hbm_src = _peaks()
     rhs_tflops = ops_cell * n_cells / (rhs64 * 1e-3) / 1e12
     rhs_gbs = bytes_cell * n_cells / (rhs64 * 1e-3) / 1e9
@@ -262,8 +296,9 @@ def run_ours(args, rank, world):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded noisy gas law, periodic 64^3 box)",
-        "config": {"workload": WORKLOAD, "subgrids": prob.n_sub, "edge": E, "ghost": 3, "n_species": 5,
+        "data": "synthetic (seeded generators of paper_2210_06439_gb300.inputs)",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; {STEP}", "subgrids": prob.n_sub,
+                   "edges": sorted(set(int(e) for e in prob.edge)), "ghost": 3, "n_species": prob.n_species,
                    "interior_cells": n_cells, "parallelism": f"replicas x{world}",
                    "l2": "flushed (256 MiB write) before each timed step"},
         "rhs": {"value": world * n_cells / (rhs64 * 1e-3), "unit": "RHS cell-updates/s", "ms": rhs64},
@@ -285,59 +320,91 @@ def run_ours(args, rank, world):
         "gpu_launches": 10 * K,
         "clocks": clocks,
         "error_flags": {"fp64": s64["flags"], "mixed": smx["flags"]},
+        "tile_mode": {"fp64": s64["tile_mode"], "mixed": smx["tile_mode"]},
     }
+    if mixed_err is not None:
+        out["mixed"]["max_rel_err_per_field_vs_oracle"] = mixed_err
     if args.cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(sample_sub=8, reps=2)
+        out["cpu_baseline"] = cpu_baseline(args.workload, reps=2)
     return out
 
 
 # ---------------------------------------------------------------------------
 # The oracle (CPU) as the reference arm and the CPU baseline
 # ---------------------------------------------------------------------------
-def _oracle_step_time(nsub):
+def mixed_error_table(prob, results, stream):
+    """Per-field max relative error of the mixed-form RHS against the FP64
+    oracle on the benchmark's own state (the CPU leg runs the oracle)."""
     import numpy as np
     import oracle
+    import torch
+    from paper_2210_06439_gb300 import binding
+    ref = prob.copy()
+    if ref.bc != 0:
+        oracle.ghost_fill(int(ref.edge[0]), ref.off, ref.nf, ref.nbr, ref.U)
+    d_o, _, _ = oracle.rhs(ref.edge, ref.off, ref.dx, ref.nf, ref.U, gamma=ref.gamma)
+    r = results[binding.OCT_MIXED]
+    r["U"].copy_(r["U0"])
+    r["H"].rhs(r["U"], r["dU"], stream=stream)
+    torch.cuda.synchronize()
+    g = r["dU"].cpu().numpy()
+    names = ["rho", "s_x", "s_y", "s_z", "E", "tau"] + [f"rho_{i + 1}" for i in range(prob.nf - 6)]
+    out = {}
+    for f in range(prob.nf):
+        idx, o = [], 0
+        for E in prob.edge:
+            E3 = int(E) ** 3
+            idx.append(np.arange(o + f * E3, o + (f + 1) * E3))
+            o += prob.nf * E3
+        idx = np.concatenate(idx)
+        m = np.max(np.abs(d_o[idx]))
+        out[names[f]] = float(np.max(np.abs(g[idx] - d_o[idx])) / m) if m > 0 else 0.0
+    return out
+
+
+def _oracle_step_time(workload):
+    import oracle
     from paper_2210_06439_gb300 import inputs
-    p = inputs.periodic_box(seed=1002, nsub=nsub)
-    oracle.ghost_fill(8, p.off, p.nf, p.nbr, p.U)
+    p = WORKLOADS[workload][2](inputs)
+    if p.bc != 0:
+        oracle.ghost_fill(int(p.edge[0]), p.off, p.nf, p.nbr, p.U)
     t0 = time.perf_counter()
-    dt, fired, st = oracle.rk3_step(p.edge, p.off, p.dx, p.nf, p.U, bc=1, nbr=p.nbr, nthreads=0)
+    dt, fired, st = oracle.rk3_step(p.edge, p.off, p.dx, p.nf, p.U, bc=p.bc, nbr=p.nbr, gamma=p.gamma, nthreads=0)
     t = time.perf_counter() - t0
-    return t, p.n_cells
+    return t, p.n_cells, p.n_sub
 
 
-def cpu_baseline(sample_sub=4, reps=1):
+def cpu_baseline(workload, reps=1):
     import oracle
     ts = []
-    cells = 0
     for _ in range(reps):
-        t, cells = _oracle_step_time(sample_sub)
+        t, cells, nsub = _oracle_step_time(workload)
         ts.append(t)
     t = min(ts)
     return {"value": cells / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"one SSP-RK3 step of the {sample_sub * 8}^3 periodic box ({sample_sub ** 3} subgrids of 8^3), "
-                      f"best of {reps}, FP64 C oracle (gcc -O2, OpenMP over subgrids)"}
+            "sample": f"one SSP-RK3 step of {nsub} subgrids ({cells} cells) of the {workload} law, best of {reps}, "
+                      "FP64 C oracle (gcc -O2, OpenMP over subgrids)"}
 
 
 def run_reference(args):
     import oracle
     oracle.build_oracle()
-    nsub = 4
     for _ in range(args.warmup):
-        _oracle_step_time(nsub)
+        _oracle_step_time(args.workload)
     ts = []
-    cells = 0
+    cells = nsub = 0
     for _ in range(args.steps):
-        t, cells = _oracle_step_time(nsub)
+        t, cells, nsub = _oracle_step_time(args.workload)
         ts.append(t)
     ms = 1e3 * sum(ts) / len(ts)
     value = cells / (ms * 1e-3)
     cb = {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-          "sample": f"one SSP-RK3 step of a {nsub * 8}^3 periodic box ({nsub ** 3} subgrids) per step, same law"}
+          "sample": f"one SSP-RK3 step of {nsub} subgrids ({cells} cells) of the {args.workload} law per step"}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "reference_sample": cb["sample"]},
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; {STEP}",
+                       "reference_sample": cb["sample"]},
             "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
 
@@ -348,6 +415,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="periodic_box_64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -191,6 +191,12 @@ oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_species, dou
                                     double de_switch1, const double *U, const double *dx, double *dUdt, double *dt,
                                     void *cuda_stream);
 
+/* Launch shape of the RHS kernel for the current layout and precision
+ * (the paper's Sec. V-B splits big kernels into tasks for the same reason:
+ * enough independent work per core): tile mode (0: 8x8-cell columns, 1:
+ * 8x4), CTAs resident per SM, and work items.  Any pointer may be NULL. */
+oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *ctas_per_sm, int *n_items);
+
 /* Reads and clears the device error flags (OCT_FLAG_*); synchronises. */
 oct_status oct_hydro_get_error_flags(oct_hydro_t h, uint32_t *flags);
 

@@ -40,6 +40,7 @@ SIGNATURES = {
     "oct_hydro_rhs_host": (_I, [_P, _P, _P, _P]),
     "oct_hydro_autotune": (_I, [_P, _P, _P]),
     "oct_hydro_rhs_dt_noalloc": (_I, [_I, _I, _I, _D, _I, _D, _D, _P, _P, _P, _P, _P]),
+    "oct_hydro_launch_info": (_I, [_P, _P, _P, _P]),
     "oct_hydro_get_error_flags": (_I, [_P, _P]),
     "oct_hydro_last_error": (ctypes.c_char_p, []),
     "oct_hydro_destroy": (None, [_P]),
@@ -190,6 +191,15 @@ class Hydro:
 
     def autotune(self, U, stream=None):
         check(self.L.oct_hydro_autotune(self.h, _ptr(U), _stream_ptr(stream)))
+
+    def launch_info(self):
+        """(tile mode, CTAs per SM, work items) of the RHS launch."""
+        t, c, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self.L.oct_hydro_launch_info(self.h, ctypes.addressof(t), ctypes.addressof(c), ctypes.addressof(n)))
+        return t.value, c.value, n.value
+
+    def tile_mode(self):
+        return self.launch_info()[0]
 
     def error_flags(self):
         v = ctypes.c_uint32()

@@ -769,6 +769,20 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
     return upload_items(h);
 }
 
+extern "C" oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *ctas_per_sm, int *n_items)
+{
+    oct_status st = check_ready(h);
+    if (st != OCT_OK)
+        return st;
+    if (tile_mode)
+        *tile_mode = h->tile_mode;
+    if (ctas_per_sm)
+        *ctas_per_sm = h->ctas_per_sm[h->precision][h->tile_mode];
+    if (n_items)
+        *n_items = (int)h->items.size();
+    return OCT_OK;
+}
+
 extern "C" oct_status oct_hydro_get_error_flags(oct_hydro_t h, uint32_t *flags)
 {
     if (!h || !flags)

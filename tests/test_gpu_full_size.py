@@ -1,0 +1,124 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times (autotuned tile shape, persistent grid over the work list,
+RK3 step replayed from the CUDA graph on a side stream).  The oracle checks
+every cell where it finishes in seconds and sampled cells elsewhere."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_06439_gb300 import inputs
+from tests.helpers import e3s, field_errors, oracle_filled
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+def _setup(prob, precision, fill=True):
+    import torch
+    from paper_2210_06439_gb300 import binding
+    H = binding.Hydro.from_problem(prob, precision=precision)
+    stream = torch.cuda.Stream()
+    U = torch.from_numpy(prob.U).cuda()
+    if fill:
+        H.fill_ghosts(U, stream=stream)
+    H.autotune(U, stream=stream)
+    return H, U, stream
+
+
+def _rhs(H, U, stream, n_sub):
+    import torch
+    d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+    am = torch.zeros(n_sub, dtype=torch.float64, device="cuda")
+    H.rhs(U, d, am, stream=stream)
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), am.cpu().numpy()
+
+
+def _sample_check(prob, d_g, n=300, seed=7, rtol=1e-11):
+    rng = np.random.default_rng(seed)
+    s = rng.integers(0, prob.n_sub, n)
+    c = np.array([rng.integers(0, int(prob.edge[k]) ** 3) for k in s])
+    smp = np.stack([s, c], axis=1)
+    ref = oracle.rhs_cells(prob.edge, prob.off, prob.dx, prob.nf, prob.U, smp, gamma=prob.gamma)
+    doff = np.concatenate([[0], np.cumsum(prob.nf * prob.edge.astype(np.int64) ** 3)])
+    worst = 0.0
+    for i, (k, cc) in enumerate(smp):
+        E3 = int(prob.edge[k]) ** 3
+        g = d_g[doff[k] + cc + E3 * np.arange(prob.nf)]
+        scale = np.maximum(np.abs(ref[i]), np.max(np.abs(ref[i])) * 1e-3)
+        worst = max(worst, float(np.max(np.abs(g - ref[i]) / scale)))
+    assert worst <= rtol, worst
+    return worst
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_periodic_box_64_autotuned(precision):
+    p = inputs.periodic_box()
+    ref = oracle_filled(p)
+    d_o, am_o, _ = oracle.rhs(ref.edge, ref.off, ref.dx, ref.nf, ref.U)
+    H, U, st = _setup(p, precision)
+    d_g, am_g = _rhs(H, U, st, p.n_sub)
+    assert H.error_flags() == 0
+    errs = field_errors(d_g, d_o, p.nf, e3s(p))
+    print(f"\nperiodic_box_64 precision={precision} max rel err per field:", " ".join(f"{e:.2e}" for e in errs))
+    assert np.all(errs <= TOL[precision]), errs
+    np.testing.assert_allclose(am_g, am_o, rtol=1e-12 if precision == 0 else 2e-6)
+
+
+def test_mixed_levels_4096_sampled():
+    p = inputs.mixed_levels()
+    H, U, st = _setup(p, 0, fill=False)
+    d_g, am_g = _rhs(H, U, st, p.n_sub)
+    assert H.error_flags() == 0
+    _sample_check(p, d_g)
+    # signal speeds of a few whole subgrids
+    for s in (0, 1, 2, 4095):
+        q = p.copy()
+        _, am_o, _ = oracle.rhs(q.edge[s:s + 1], q.off[s:s + 1], q.dx[s:s + 1], q.nf, q.U)
+        assert am_g[s] == pytest.approx(am_o[0], rel=1e-12)
+
+
+def test_binary_star_128_fp64_and_mixed_error_table():
+    p = inputs.binary_star(16)
+    ref = oracle_filled(p)
+    d_o, am_o, nb = oracle.rhs(ref.edge, ref.off, ref.dx, ref.nf, ref.U)
+    assert nb == 0
+    rows = {}
+    for prec in (0, 1):
+        H, U, st = _setup(p, prec)
+        d_g, am_g = _rhs(H, U, st, p.n_sub)
+        assert H.error_flags() == 0
+        rows[prec] = field_errors(d_g, d_o, p.nf, e3s(p))
+        np.testing.assert_allclose(am_g, am_o, rtol=1e-12 if prec == 0 else 2e-6)
+    names = ["rho", "sx", "sy", "sz", "E", "tau", "r1", "r2", "r3", "r4", "r5"]
+    print("\nbinary_star_128 max rel err per field (FP64 | mixed):")
+    for f in range(p.nf):
+        print(f"  {names[f]:4s} {rows[0][f]:.2e} | {rows[1][f]:.2e}")
+    assert np.all(rows[0] <= TOL[0]) and np.all(rows[1] <= TOL[1])
+
+
+def test_binary_star_256_graph_steps():
+    import torch
+    p = inputs.binary_star(32)
+    # RHS parity on the initial state at sampled cells (oracle fills its own ghosts)
+    ref = oracle_filled(p)
+    H, U, st = _setup(p, 0)
+    d_g, _ = _rhs(H, U, st, p.n_sub)
+    assert H.error_flags() == 0
+    _sample_check(ref, d_g, n=200)
+    del d_g, ref
+    # a few RK3 steps from the captured graph, in both forms
+    for prec in (0, 1):
+        if prec == 1:
+            H.close()
+            H, U, st = _setup(p, 1)
+        mass0 = float(torch.sum(U).item())
+        dts = [H.rk_step(U, stream=st) for _ in range(4)]
+        torch.cuda.synchronize()
+        assert H.error_flags() == 0
+        assert all(d > 0 and math.isfinite(d) for d in dts)
+        assert torch.isfinite(U).all().item()
+        assert math.isfinite(float(torch.sum(U).item())) and mass0 > 0
