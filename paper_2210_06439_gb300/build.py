@@ -1,7 +1,9 @@
 """Builds the sm_103a CUDA library liboct_hydro.so in-tree with nvcc.
 
-One translation unit (the kernels are header templates included by the ABI
-file), compiled for compute_103a/sm_103a only."""
+The four RHS kernel instances (FP64 / mixed, tile capacity 8x8 / 8x4) are
+separate translation units; they and the host side compile in parallel to
+objects, which nvcc then links into one shared library (static CUDA
+runtime).  Only compute_103a/sm_103a code is generated."""
 from __future__ import annotations
 
 import os
@@ -12,15 +14,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboct_hydro.so")
-MAIN = os.path.join(SRC_DIR, "oct_hydro.cu")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include", "oct_hydro.h")
+UNITS = ["oct_hydro.cu", "rhs_dispatch.cu", "rhs_fp64_m0.cu", "rhs_fp64_m1.cu", "rhs_mixed_m0.cu",
+         "rhs_mixed_m1.cu"]
 
-NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-shared"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 
 def _sources():
-    return [os.path.join(SRC_DIR, f) for f in os.listdir(SRC_DIR) if f.endswith((".cu", ".cuh"))] + [INCLUDE]
+    return [os.path.join(SRC_DIR, f) for f in os.listdir(SRC_DIR) if f.endswith((".cu", ".cuh", ".h"))] + [INCLUDE]
 
 
 def nvcc() -> str:
@@ -37,13 +40,31 @@ def build(force: bool = False, verbose: bool = False) -> str:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(s) <= t for s in _sources()):
             return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc()] + NVCC_FLAGS + [MAIN, "-o", tmp]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    tag = f".{os.getpid()}"
+    objs, procs = [], []
+    for u in UNITS:
+        o = os.path.join(OUT_DIR, u.replace(".cu", "") + tag.replace(".", "_") + ".o")
+        objs.append(o)
+        cmd = [nvcc()] + NVCC_FLAGS + ["-c", os.path.join(SRC_DIR, u), "-o", o]
+        procs.append((u, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+    errors = []
+    for u, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            errors.append(f"{u}:\n{out}")
+        elif verbose and out:
+            print(out)
+    if errors:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
+        raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
+    tmp = LIB + tag + ".so"
+    r = subprocess.run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
+    for o in objs:
+        os.remove(o)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
-    if verbose:
-        print(r.stdout + r.stderr)
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB)
     return LIB
 

@@ -10,6 +10,7 @@ constexpr int MAXNF = 11;   // 6 hydro fields + up to 5 species
 constexpr int MAXT = 8;     // max tile edge (x and y) of one work item
 constexpr int NTHREADS = 256;
 
+
 enum { F_RHO = 0, F_SX = 1, F_SY = 2, F_SZ = 3, F_EGAS = 4, F_TAU = 5, F_SPC = 6 };
 
 // One work item of the RHS kernel: a column of a subgrid, tx * ty cells in
@@ -35,6 +36,8 @@ struct GroupTab {
     int nzp;                       // +z ends this group leaves for the next plane
     signed char zp_src[4], zp_dst[4];
     int has[3];                    // group has lines with a nonzero x / y / z step
+    int napt;                      // face points per face (the same for every axis of the group)
+    signed char apt[3][4];         // indices into the point arrays, per face axis
 };
 constexpr int NGROUPS = 7;
 

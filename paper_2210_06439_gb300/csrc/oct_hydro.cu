@@ -15,7 +15,7 @@
 
 #include "../../include/oct_hydro.h"
 #include "oct_common.cuh"
-#include "rhs_kernel.cuh"
+#include "rhs_launch.h"
 #include "step_kernels.cuh"
 
 using namespace octh;
@@ -40,75 +40,6 @@ static oct_status fail(oct_status st, const char *fmt, ...)
             return fail(e_ == cudaErrorMemoryAllocation ? OCT_E_NOMEM : OCT_E_CUDA, "%s: %s (%s:%d)", #call, \
                         cudaGetErrorString(e_), __FILE__, __LINE__);                                     \
     } while (0)
-
-// ---------------------------------------------------------------------------
-// Line-group tables (see rhs_kernel.cuh)
-// ---------------------------------------------------------------------------
-static void canon(const int *d, int *line, int *end)
-{
-    int first = d[0] ? d[0] : (d[1] ? d[1] : d[2]);
-    int sg = first > 0 ? 1 : -1;
-    for (int a = 0; a < 3; a++)
-        line[a] = d[a] * sg;
-    *end = first > 0 ? 1 : 0;
-}
-
-static std::vector<GroupTab> build_groups()
-{
-    static const int L[13][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1},
-                                 {0, 1, 1}, {0, 1, -1}, {1, 1, 1}, {1, -1, -1}, {1, -1, 1}, {1, 1, -1}};
-    static const int GL[NGROUPS][5] = {{1, 0}, {1, 1}, {1, 2}, {2, 3, 4}, {2, 5, 6}, {2, 7, 8}, {4, 9, 10, 11, 12}};
-    std::vector<GroupTab> gs(NGROUPS);
-    for (int g = 0; g < NGROUPS; g++) {
-        GroupTab &G = gs[g];
-        memset(&G, 0, sizeof G);
-        G.nl = GL[g][0];
-        for (int l = 0; l < G.nl; l++)
-            for (int a = 0; a < 3; a++) {
-                G.line[l][a] = L[GL[g][1 + l]][a];
-                if (G.line[l][a])
-                    G.has[a] = 1;
-            }
-        auto find = [&](const int *d) -> int {
-            int ln[3], e;
-            canon(d, ln, &e);
-            for (int l = 0; l < G.nl; l++)
-                if (ln[0] == G.line[l][0] && ln[1] == G.line[l][1] && ln[2] == G.line[l][2])
-                    return 2 * l + e;
-            return -1;
-        };
-        for (int k = 0; k < 3; k++) {
-            int a1 = (k == 0) ? 1 : 0, a2 = (k == 2) ? 1 : 2;
-            for (int t2 = -1; t2 <= 1; t2++)
-                for (int t1 = -1; t1 <= 1; t1++) {
-                    int dL[3] = {0, 0, 0}, dR[3] = {0, 0, 0};
-                    dL[k] = 1;
-                    dR[k] = -1;
-                    dL[a1] = dR[a1] = t1;
-                    dL[a2] = dR[a2] = t2;
-                    int ls = find(dL), rs = find(dR);
-                    if (ls < 0 || rs < 0)
-                        continue;
-                    int p = G.npt++;
-                    G.axis[p] = (signed char)k;
-                    G.wcls[p] = (signed char)((t1 != 0) + (t2 != 0));
-                    G.rslot[p] = (signed char)rs;
-                    G.lslot[p] = (signed char)(k == 2 ? 16 + (t2 + 1) * 3 + (t1 + 1) : ls);
-                }
-        }
-        for (int l = 0; l < G.nl; l++) {
-            if (!G.line[l][2])
-                continue;
-            int end = G.line[l][2] > 0 ? 1 : 0;
-            int sg = end ? 1 : -1;
-            int dxe = G.line[l][0] * sg, dye = G.line[l][1] * sg;
-            G.zp_src[G.nzp] = (signed char)(2 * l + end);
-            G.zp_dst[G.nzp] = (signed char)((dye + 1) * 3 + (dxe + 1));
-            G.nzp++;
-        }
-    }
-    return gs;
-}
 
 // ---------------------------------------------------------------------------
 // Handle
@@ -146,22 +77,6 @@ struct oct_hydro {
     std::map<const double *, GraphEntry> graphs;
 };
 
-static bool g_tables_ready[64];
-
-static oct_status ensure_tables(int dev)
-{
-    if (dev >= 0 && dev < 64 && g_tables_ready[dev])
-        return OCT_OK;
-    std::vector<GroupTab> gs = build_groups();
-    CUDA_TRY(cudaMemcpyToSymbol(c_groups, gs.data(), sizeof(GroupTab) * NGROUPS));
-    for (int T = 0; T < 2; T++) {
-        (void)T;
-    }
-    if (dev >= 0 && dev < 64)
-        g_tables_ready[dev] = true;
-    return OCT_OK;
-}
-
 template <class P>
 static void dfree(P *&p)
 {
@@ -195,45 +110,15 @@ static void free_layout(oct_hydro *h)
     drop_graphs(h);
 }
 
-// RHS kernel instances: tile capacity 8x8 (one CTA per SM) or 8x4 (two).
-static size_t rhs_smem_of(int nf, int prec, int mode)
-{
-    return smem_plan(nf, prec == OCT_FP64 ? 8 : 4, prec != OCT_FP64, 8, mode == 0 ? 8 : 4).total;
-}
-
-static const void *rhs_fn(int prec, int mode)
-{
-    if (prec == OCT_FP64)
-        return mode == 0 ? (const void *)rhs_kernel<double, false, 8, 8, 1> : (const void *)rhs_kernel<double, false, 8, 4, 2>;
-    return mode == 0 ? (const void *)rhs_kernel<float, true, 8, 8, 1> : (const void *)rhs_kernel<float, true, 8, 4, 2>;
-}
-
-static void rhs_launch(int prec, int mode, int grid, size_t sm, cudaStream_t st, const RhsArgs &A)
-{
-    if (prec == OCT_FP64) {
-        if (mode == 0)
-            rhs_kernel<double, false, 8, 8, 1><<<grid, NTHREADS, sm, st>>>(A);
-        else
-            rhs_kernel<double, false, 8, 4, 2><<<grid, NTHREADS, sm, st>>>(A);
-    } else {
-        if (mode == 0)
-            rhs_kernel<float, true, 8, 8, 1><<<grid, NTHREADS, sm, st>>>(A);
-        else
-            rhs_kernel<float, true, 8, 4, 2><<<grid, NTHREADS, sm, st>>>(A);
-    }
-}
-
 static oct_status set_kernel_attrs(oct_hydro *h)
 {
     for (int prec = 0; prec < 2; prec++)
         for (int mode = 0; mode < 2; mode++) {
-            size_t sm = rhs_smem_of(h->nf, prec, mode);
-            const void *fn = rhs_fn(prec, mode);
-            CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             int nb = 0;
-            CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NTHREADS, sm));
+            CUDA_TRY(rhs_prepare(prec, mode, h->nf, &nb));
             if (nb < 1)
-                return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM (%zu bytes shared memory)", sm);
+                return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM (%zu bytes shared memory)",
+                            rhs_smem_bytes(h->nf, prec, mode));
             h->ctas_per_sm[prec][mode] = nb;
         }
     return OCT_OK;
@@ -311,9 +196,7 @@ extern "C" oct_status oct_hydro_create(int n_subgrids, int edge, int ghost, int 
         delete h;
         return fail(OCT_E_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
     }
-    oct_status st = ensure_tables(h->device);
-    if (st == OCT_OK)
-        st = set_kernel_attrs(h);
+    oct_status st = set_kernel_attrs(h);
     if (st == OCT_OK && cudaMalloc(&h->d_flags, sizeof(unsigned)) != cudaSuccess)
         st = fail(OCT_E_NOMEM, "cudaMalloc flags");
     if (st == OCT_OK && cudaMemset(h->d_flags, 0, sizeof(unsigned)) != cudaSuccess)
@@ -510,7 +393,7 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
     A.flags = h->d_flags;
     const int prec = h->precision, mode = h->tile_mode;
     int grid = std::min<int>(A.n_items, h->n_sm * h->ctas_per_sm[prec][mode]);
-    rhs_launch(prec, mode, grid, rhs_smem_of(h->nf, prec, mode), st, A);
+    CUDA_TRY(rhs_launch(prec, mode, grid, st, A));
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;
 }
@@ -885,16 +768,10 @@ static oct_status noalloc_setup(int dev, NoallocDevice **out)
     if (!d.ready) {
         void *p = nullptr;
         CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        oct_status st = ensure_tables(dev);
-        if (st != OCT_OK)
-            return st;
         CUDA_TRY(cudaDeviceGetAttribute(&d.n_sm, cudaDevAttrMultiProcessorCount, dev));
         for (int prec = 0; prec < 2; prec++) {
-            size_t sm = rhs_smem_of(MAXNF, prec, 0);
-            const void *fn = rhs_fn(prec, 0);
-            CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             int nb = 0;
-            CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NTHREADS, sm));
+            CUDA_TRY(rhs_prepare(prec, 0, MAXNF, &nb));
             if (nb < 1)
                 return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM");
             d.ctas[prec] = nb;
@@ -975,10 +852,8 @@ extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_s
     A.gamma = gamma;
     A.eps1 = de_switch1;
     A.flags = flags;
-    size_t sm = rhs_smem_of(nf, precision, 0);
     int grid = std::min(n_items, D->n_sm * D->ctas[precision]);
-    rhs_launch(precision, 0, grid, sm, s, A);
-    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(rhs_launch(precision, 0, grid, s, A));
     dt_kernel<<<1, 1024, 0, s>>>(n_items, d_items, dx, d_amax, cfl, 0.0, dt);
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;

@@ -1,0 +1,114 @@
+// rhs_dispatch.cu -- selects the RHS kernel instance of a precision and tile mode.
+#include <cstring>
+
+#include "rhs_kernel.cuh"
+#include "rhs_launch.h"
+
+namespace octh {
+
+static void canon(const int *d, int *line, int *end)
+{
+    int first = d[0] ? d[0] : (d[1] ? d[1] : d[2]);
+    int sg = first > 0 ? 1 : -1;
+    for (int a = 0; a < 3; a++)
+        line[a] = d[a] * sg;
+    *end = first > 0 ? 1 : 0;
+}
+
+// The 13 PPM lines in 7 groups (x, y, z, xy, xz, yz, body diagonals) and,
+// per group, its face quadrature points, per-axis point lists and the +z ends
+// it carries to the next plane (see rhs_kernel.cuh).
+bool build_group_tables(GroupTab *gs)
+{
+    static const int L[13][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1},
+                                 {0, 1, 1}, {0, 1, -1}, {1, 1, 1}, {1, -1, -1}, {1, -1, 1}, {1, 1, -1}};
+    static const int GL[NGROUPS][5] = {{1, 0}, {1, 1}, {1, 2}, {2, 3, 4}, {2, 5, 6}, {2, 7, 8}, {4, 9, 10, 11, 12}};
+    for (int g = 0; g < NGROUPS; g++) {
+        GroupTab &G = gs[g];
+        memset(&G, 0, sizeof G);
+        G.nl = GL[g][0];
+        for (int l = 0; l < G.nl; l++)
+            for (int a = 0; a < 3; a++) {
+                G.line[l][a] = L[GL[g][1 + l]][a];
+                if (G.line[l][a])
+                    G.has[a] = 1;
+            }
+        auto find = [&](const int *d) -> int {
+            int ln[3], e;
+            canon(d, ln, &e);
+            for (int l = 0; l < G.nl; l++)
+                if (ln[0] == G.line[l][0] && ln[1] == G.line[l][1] && ln[2] == G.line[l][2])
+                    return 2 * l + e;
+            return -1;
+        };
+        for (int k = 0; k < 3; k++) {
+            int a1 = (k == 0) ? 1 : 0, a2 = (k == 2) ? 1 : 2;
+            for (int t2 = -1; t2 <= 1; t2++)
+                for (int t1 = -1; t1 <= 1; t1++) {
+                    int dL[3] = {0, 0, 0}, dR[3] = {0, 0, 0};
+                    dL[k] = 1;
+                    dR[k] = -1;
+                    dL[a1] = dR[a1] = t1;
+                    dL[a2] = dR[a2] = t2;
+                    int ls = find(dL), rs = find(dR);
+                    if (ls < 0 || rs < 0)
+                        continue;
+                    int p = G.npt++;
+                    G.axis[p] = (signed char)k;
+                    G.wcls[p] = (signed char)((t1 != 0) + (t2 != 0));
+                    G.rslot[p] = (signed char)rs;
+                    G.lslot[p] = (signed char)(k == 2 ? 16 + (t2 + 1) * 3 + (t1 + 1) : ls);
+                }
+        }
+        int cnt[3] = {0, 0, 0};
+        for (int p = 0; p < G.npt; p++) {
+            int k = G.axis[p];
+            G.apt[k][cnt[k]++] = (signed char)p;
+        }
+        G.napt = cnt[0] > cnt[1] ? (cnt[0] > cnt[2] ? cnt[0] : cnt[2]) : (cnt[1] > cnt[2] ? cnt[1] : cnt[2]);
+        for (int k = 0; k < 3; k++)
+            if (cnt[k] != 0 && cnt[k] != G.napt)
+                return false;  // the uniform point loop of the kernel needs equal counts
+        for (int l = 0; l < G.nl; l++) {
+            if (!G.line[l][2])
+                continue;
+            int end = G.line[l][2] > 0 ? 1 : 0;
+            int sg = end ? 1 : -1;
+            int dxe = G.line[l][0] * sg, dye = G.line[l][1] * sg;
+            G.zp_src[G.nzp] = (signed char)(2 * l + end);
+            G.zp_dst[G.nzp] = (signed char)((dye + 1) * 3 + (dxe + 1));
+            G.nzp++;
+        }
+    }
+    return true;
+}
+
+cudaError_t rhs_prepare_fp64_m0(int nf, int *ctas_per_sm);
+cudaError_t rhs_prepare_fp64_m1(int nf, int *ctas_per_sm);
+cudaError_t rhs_prepare_mixed_m0(int nf, int *ctas_per_sm);
+cudaError_t rhs_prepare_mixed_m1(int nf, int *ctas_per_sm);
+cudaError_t rhs_launch_fp64_m0(int grid, cudaStream_t stream, const RhsArgs &args);
+cudaError_t rhs_launch_fp64_m1(int grid, cudaStream_t stream, const RhsArgs &args);
+cudaError_t rhs_launch_mixed_m0(int grid, cudaStream_t stream, const RhsArgs &args);
+cudaError_t rhs_launch_mixed_m1(int grid, cudaStream_t stream, const RhsArgs &args);
+
+size_t rhs_smem_bytes(int nf, int precision, int mode)
+{
+    return smem_plan(nf, precision == 0 ? 8 : 4, precision != 0, 8, mode == 0 ? 8 : 4).total;
+}
+
+cudaError_t rhs_prepare(int precision, int mode, int nf, int *ctas_per_sm)
+{
+    if (precision == 0)
+        return mode == 0 ? rhs_prepare_fp64_m0(nf, ctas_per_sm) : rhs_prepare_fp64_m1(nf, ctas_per_sm);
+    return mode == 0 ? rhs_prepare_mixed_m0(nf, ctas_per_sm) : rhs_prepare_mixed_m1(nf, ctas_per_sm);
+}
+
+cudaError_t rhs_launch(int precision, int mode, int grid, cudaStream_t stream, const RhsArgs &args)
+{
+    if (precision == 0)
+        return mode == 0 ? rhs_launch_fp64_m0(grid, stream, args) : rhs_launch_fp64_m1(grid, stream, args);
+    return mode == 0 ? rhs_launch_mixed_m0(grid, stream, args) : rhs_launch_mixed_m1(grid, stream, args);
+}
+
+}  // namespace octh

@@ -501,44 +501,55 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                     temp[((2 * l + 1) * nf + f) * NC + ci] = vp;
                 }
                 __syncthreads();
-                // ---- phase B1: primitives of every needed point of the group ----
+                // ---- phase B1: primitives of every needed point of the group:
+                // both ends of interior cells (one end in the boundary planes),
+                // the inward end of ring cells ----
                 {
-                    const int tot = 2 * (n0 + n1 + n2 + n3);
+                    const int per_in = inplane ? 2 * ncin : ncin;
+                    const int m0 = per_in + (n0 - ncin), m1 = nl > 1 ? per_in + (n1 - ncin) : 0,
+                              m2 = nl > 2 ? per_in + (n2 - ncin) : 0, m3 = nl > 3 ? per_in + (n3 - ncin) : 0;
+                    const int tot = m0 + m1 + m2 + m3;
                     for (int q = tid; q < tot; q += NTHREADS) {
-                        int l = 0, r = q, t = t0, n = n0;
-                        if (r >= 2 * n0) {
-                            r -= 2 * n0;
-                            l = 1, t = t1, n = n1;
-                            if (r >= 2 * n1) {
-                                r -= 2 * n1;
-                                l = 2, t = t2, n = n2;
-                                if (r >= 2 * n2) {
-                                    r -= 2 * n2;
-                                    l = 3, t = t3, n = n3;
+                        int l = 0, r = q, t = t0;
+                        if (r >= m0) {
+                            r -= m0;
+                            l = 1, t = t1;
+                            if (r >= m1) {
+                                r -= m1;
+                                l = 2, t = t2;
+                                if (r >= m2) {
+                                    r -= m2;
+                                    l = 3, t = t3;
                                 }
                             }
                         }
-                        const int e = r >= n;
-                        const int c = r - e * n;
+                        const int lx = G.line[l][0], ly = G.line[l][1], lz = G.line[l][2];
+                        int c, e;
+                        if (r < per_in) {
+                            if (inplane) {
+                                c = r >> 1;
+                                e = r & 1;
+                            } else {
+                                c = r;
+                                // boundary planes: the end facing the interior (+z below, -z above)
+                                e = ((kz < 0) == (lz > 0)) ? 1 : 0;
+                            }
+                        } else {
+                            c = ncin + (r - per_in);
+                        }
                         const int info = lists[t * NC + c];
                         const int i = (info & 0xFF) - 1, j = ((info >> 8) & 0xFF) - 1, ci = info >> 16;
-                        const int sg = e ? 1 : -1;  // direction of this end = sg * line
-                        const int ex = sg * G.line[l][0], ey = sg * G.line[l][1], ez = sg * G.line[l][2];
-                        bool need;
-                        if (!inplane)
-                            need = (kz < 0) ? (ez == 1) : (ez == -1);
-                        else if (i < 0)
-                            need = ex == 1;
-                        else if (i >= tx)
-                            need = ex == -1;
-                        else if (j < 0)
-                            need = ey == 1;
-                        else if (j >= ty)
-                            need = ey == -1;
-                        else
-                            need = true;
-                        if (!need)
-                            continue;
+                        if (r >= per_in) {
+                            // ring cell: the end pointing into the tile
+                            if (i < 0)
+                                e = lx > 0 ? 1 : 0;
+                            else if (i >= tx)
+                                e = lx > 0 ? 0 : 1;
+                            else if (j < 0)
+                                e = ly > 0 ? 1 : 0;
+                            else
+                                e = ly > 0 ? 0 : 1;
+                        }
                         const int slot = 2 * l + e;
                         T qh[6];
 #pragma unroll
@@ -556,43 +567,37 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                 }
                 __syncthreads();
                 // ---- phase B2: KT flux at the group's points, one thread per face;
-                // warp-aligned ranges of threads for x, y and z faces ----
+                // the faces of the group's axes packed densely (every face of the
+                // group has the same number of points, so the point loop is uniform) ----
                 {
-                    int axis, cl = 0, cr = 0, fslot = 0;
-                    bool act;
-                    if (tid < XW) {
+                    const int nfx = (inplane && G.has[0]) ? (tx + 1) * ty : 0;
+                    const int nfy = (inplane && G.has[1]) ? tx * (ty + 1) : 0;
+                    const int nfz = G.has[2] ? ncin : 0;
+                    int axis = 2, cl = 0, cr = 0, fslot = 0;
+                    const bool act = tid < nfx + nfy + nfz;
+                    if (tid < nfx) {
                         axis = 0;
-                        act = inplane && G.has[0] && tid < (tx + 1) * ty;
-                        if (act) {
-                            int p = tid % (tx + 1), j = tid / (tx + 1);
-                            cl = cidx(p - 1, j, tx, ty);
-                            cr = cidx(p, j, tx, ty);
-                            fslot = tid;
-                        }
-                    } else if (tid < XW + YW) {
+                        int p = tid % (tx + 1), j = tid / (tx + 1);
+                        cl = cidx(p - 1, j, tx, ty);
+                        cr = cidx(p, j, tx, ty);
+                        fslot = tid;
+                    } else if (tid < nfx + nfy) {
                         axis = 1;
-                        int r = tid - XW;
-                        act = inplane && G.has[1] && r < tx * (ty + 1);
-                        if (act) {
-                            int i = r % tx, p = r / tx;
-                            cl = cidx(i, p - 1, tx, ty);
-                            cr = cidx(i, p, tx, ty);
-                            fslot = r;
-                        }
-                    } else {
-                        axis = 2;
-                        int r = tid - XW - YW;
-                        act = G.has[2] && r < ncin;
-                        cl = cr = fslot = r;
+                        int r = tid - nfx;
+                        int i = r % tx, p = r / tx;
+                        cl = cidx(i, p - 1, tx, ty);
+                        cr = cidx(i, p, tx, ty);
+                        fslot = r;
+                    } else if (act) {
+                        cl = cr = fslot = tid - nfx - nfy;
                     }
                     if (act && (axis < 2 || kz >= 0)) {
                         T acc[MAXNF];
 #pragma unroll
                         for (int f = 0; f < MAXNF; f++)
                             acc[f] = T(0);
-                        for (int pt = 0; pt < G.npt; pt++) {
-                            if (G.axis[pt] != axis)
-                                continue;
+                        for (int k = 0; k < G.napt; k++) {
+                            const int pt = G.apt[axis][k];
                             const T w = G.wcls[pt] == 0 ? T(16.0 / 36.0) : (G.wcls[pt] == 1 ? T(4.0 / 36.0) : T(1.0 / 36.0));
                             const int ls = G.lslot[pt], rs = G.rslot[pt];
                             const T *qL, *pL_;

@@ -1,0 +1,18 @@
+// rhs_launch.h -- host launchers of the RHS kernel instances.  Each instance
+// (FP64 or mixed, tile capacity 8x8 or 8x4) is compiled in a translation unit
+// of its own (rhs_<form>_<capacity>.cu) so the four build in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "oct_common.cuh"
+
+namespace octh {
+
+// precision: 0 FP64, 1 mixed; mode: 0 tile capacity 8x8 (one CTA per SM),
+// 1 capacity 8x4 (two CTAs per SM).
+size_t rhs_smem_bytes(int nf, int precision, int mode);
+bool build_group_tables(GroupTab *groups);
+cudaError_t rhs_prepare(int precision, int mode, int nf, int *ctas_per_sm);
+cudaError_t rhs_launch(int precision, int mode, int grid, cudaStream_t stream, const RhsArgs &args);
+
+}  // namespace octh
