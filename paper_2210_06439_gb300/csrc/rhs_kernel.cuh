@@ -25,6 +25,8 @@
 // divergence of a plane is finished one plane later, once its upper z face
 // is known.  The signal speed max over all face points is reduced per item.
 #pragma once
+#include <utility>
+
 #include "oct_common.cuh"
 
 namespace octh {
@@ -309,8 +311,9 @@ __host__ __device__ inline SmemPlan smem_plan(int nf, int elem, bool staged, int
     auto take = [&](size_t bytes) { size_t at = o; o += (bytes + 15) / 16 * 16; return at; };
     p.temp = take((size_t)8 * nf * p.nc * elem);
     p.saved = take((size_t)9 * nf * cin * elem);
-    p.pr = take((size_t)8 * 5 * p.nc * elem);
-    p.prs = take((size_t)9 * 5 * cin * elem);
+    const bool shared_prims = elem == 8;  // FP32 recomputes primitives per face point
+    p.pr = shared_prims ? take((size_t)8 * 5 * p.nc * elem) : 0;
+    p.prs = shared_prims ? take((size_t)9 * 5 * cin * elem) : 0;
     p.faccx = take((size_t)nf * (txm + 1) * tym * elem);
     p.faccy = take((size_t)nf * txm * (tym + 1) * elem);
     p.zacc = take((size_t)2 * nf * cin * elem);
@@ -337,10 +340,90 @@ __device__ __forceinline__ int cidx(int i, int j, int tx, int ty)
     return tx * ty + 2 * ty + tx + i;
 }
 
+// Compile-time line geometry of group g (the same grouping as the host's
+// table): 0 x, 1 y, 2 z, 3 xy diagonals, 4 xz, 5 yz, 6 body diagonals.
+__host__ __device__ constexpr int gnl(int g) { return g < 3 ? 1 : (g < 6 ? 2 : 4); }
+__host__ __device__ constexpr int gline(int g, int l, int a)
+{
+    return g == 0   ? (a == 0 ? 1 : 0)
+           : g == 1 ? (a == 1 ? 1 : 0)
+           : g == 2 ? (a == 2 ? 1 : 0)
+           : g == 3 ? (a == 0 ? 1 : a == 1 ? (l == 0 ? 1 : -1) : 0)
+           : g == 4 ? (a == 0 ? 1 : a == 2 ? (l == 0 ? 1 : -1) : 0)
+           : g == 5 ? (a == 1 ? 1 : a == 2 ? (l == 0 ? 1 : -1) : 0)
+                    : (a == 0 ? 1 : a == 1 ? ((l == 0 || l == 3) ? 1 : -1) : ((l == 0 || l == 2) ? 1 : -1));
+}
+
+template <class F, int... I>
+__device__ __forceinline__ void sfor_impl(F &&f, std::integer_sequence<int, I...>)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+// calls f(integral_constant<int, i>) for i = 0 .. N-1
+template <int N, class F>
+__device__ __forceinline__ void sfor(F &&f)
+{
+    sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// Phase A of line group G: 1-D PPM of every (line, field, cell), both ends
+// into the group buffer.  The line steps are compile-time constants; the
+// items are ordered line, field, cell.
+template <class T, bool STAGED, int G>
+__device__ __forceinline__ void phase_a(T *temp, const float *raw, const double *Ub, long long FS, int B, int x0,
+                                        int y0, int kz, bool inplane, int nf, int NC, int RWX, int plane,
+                                        const int *lists, const int *nlist, const unsigned *magic, const int *so,
+                                        int tid)
+{
+    constexpr int NL = gnl(G);
+    constexpr int LX = gline(G, 0, 0) != 0, LY = gline(G, 0, 1) != 0;
+    const int t = inplane ? (LX | (LY << 1)) : 0;
+    const int n = nlist[t];
+    const unsigned mg = magic[t];
+    const int per = n * nf;
+    const int *lst = lists + t * NC;
+    for (int q = tid; q < NL * per; q += NTHREADS) {
+        sfor<NL>([&](auto Lc) {
+            constexpr int L = decltype(Lc)::value;
+            if (q >= L * per && q < (L + 1) * per) {
+                constexpr int dx = gline(G, L, 0), dy = gline(G, L, 1), dz = gline(G, L, 2);
+                const int r = q - L * per;
+                const int f = __umulhi((unsigned)r, mg);
+                const int c = r - f * n;
+                const int info = lst[c];
+                const int i = (info & 0xFF) - 1, j = ((info >> 8) & 0xFF) - 1, ci = info >> 16;
+                T u[5];
+                if constexpr (STAGED) {
+                    const float *rb = raw + f * plane + (j + NG) * RWX + (i + NG);
+                    const int step = dy * RWX + dx;
+#pragma unroll
+                    for (int m = -2; m <= 2; m++)
+                        u[m + 2] = (T)rb[so[dz > 0 ? m + 2 : (dz < 0 ? 2 - m : 2)] + m * step];
+                } else {
+                    const long long st = (long long)dz * B * B + (long long)dy * B + dx;
+                    const double *ub =
+                        Ub + f * FS + (long long)(kz + NG) * B * B + (long long)(y0 + j + NG) * B + (x0 + i + NG);
+#pragma unroll
+                    for (int m = -2; m <= 2; m++)
+                        u[m + 2] = Num<T>::from_d(__ldg(ub + m * st));
+                }
+                T vm, vp;
+                ppm5<T>(u[0], u[1], u[2], u[3], u[4], vm, vp);
+                temp[((2 * L) * nf + f) * NC + ci] = vm;
+                temp[((2 * L + 1) * nf + f) * NC + ci] = vp;
+            }
+        });
+    }
+}
+
 template <class T, bool STAGED, int TXM, int TYM, int MINB>
 __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    // FP64: primitives once per point, shared through shared memory (FP64
+    // arithmetic is scarce); FP32: recomputed at each face point (cheap), which
+    // saves a phase and its barrier per line group
+    constexpr bool SHARED_PRIMS = sizeof(T) == 8;
     const int nf = A.nf;
     const SmemPlan P = smem_plan(nf, sizeof(T), STAGED, TXM, TYM);
     constexpr int NC = TXM * TYM + 2 * TXM + 2 * TYM;
@@ -458,49 +541,23 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                           n3 = nl > 3 ? nlist[t3] : 0;
                 const int totA = (n0 + n1 + n2 + n3) * nf;
                 // ---- phase A: 1-D PPM for every (line, field, cell) of the group ----
-                for (int q = tid; q < totA; q += NTHREADS) {
-                    int l = 0, r = q, t = t0, n = n0;
-                    if (r >= n0 * nf) {
-                        r -= n0 * nf;
-                        l = 1, t = t1, n = n1;
-                        if (r >= n1 * nf) {
-                            r -= n1 * nf;
-                            l = 2, t = t2, n = n2;
-                            if (r >= n2 * nf) {
-                                r -= n2 * nf;
-                                l = 3, t = t3, n = n3;
-                            }
-                        }
-                    }
-                    const unsigned mg = t == 0 ? magic[0] : (t == 1 ? magic[1] : (t == 2 ? magic[2] : magic[3]));
-                    const int f = __umulhi((unsigned)r, mg);
-                    const int c = r - f * n;
-                    const int info = lists[t * NC + c];
-                    const int i = (info & 0xFF) - 1, j = ((info >> 8) & 0xFF) - 1, ci = info >> 16;
-                    const int ddx = G.line[l][0], ddy = G.line[l][1], ddz = G.line[l][2];
-                    T u[5];
-                    if constexpr (STAGED) {
-                        const float *rb = raw + f * RWY * RWX + (j + NG) * RWX + (i + NG);
-                        const int step = ddy * RWX + ddx;
-#pragma unroll
-                        for (int m = -2; m <= 2; m++) {
-                            const int pz = ddz > 0 ? so[m + 2] : (ddz < 0 ? so[2 - m] : so[2]);
-                            u[m + 2] = (T)rb[pz + m * step];
-                        }
-                    } else {
-                        const long long st = (long long)ddz * B * B + (long long)ddy * B + ddx;
-                        const double *ub = Ub + f * FS + (long long)(kz + NG) * B * B + (long long)(y0 + j + NG) * B +
-                                           (x0 + i + NG);
-#pragma unroll
-                        for (int m = -2; m <= 2; m++)
-                            u[m + 2] = Num<T>::from_d(__ldg(ub + m * st));
-                    }
-                    T vm, vp;
-                    ppm5<T>(u[0], u[1], u[2], u[3], u[4], vm, vp);
-                    temp[((2 * l) * nf + f) * NC + ci] = vm;
-                    temp[((2 * l + 1) * nf + f) * NC + ci] = vp;
+                switch (g) {
+#define OCT_PHASE_A(GG)                                                                                              \
+    case GG:                                                                                                         \
+        phase_a<T, STAGED, GG>(temp, raw, Ub, FS, B, x0, y0, kz, inplane, nf, NC, RWX, RWY * RWX, lists, nlist,     \
+                               magic, so, tid);                                                                      \
+        break;
+                    OCT_PHASE_A(0)
+                    OCT_PHASE_A(1)
+                    OCT_PHASE_A(2)
+                    OCT_PHASE_A(3)
+                    OCT_PHASE_A(4)
+                    OCT_PHASE_A(5)
+                    OCT_PHASE_A(6)
+#undef OCT_PHASE_A
                 }
                 __syncthreads();
+                if constexpr (SHARED_PRIMS) {
                 // ---- phase B1: primitives of every needed point of the group:
                 // both ends of interior cells (one end in the boundary planes),
                 // the inward end of ring cells ----
@@ -566,6 +623,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                     }
                 }
                 __syncthreads();
+                }
                 // ---- phase B2: KT flux at the group's points, one thread per face;
                 // the faces of the group's axes packed densely (every face of the
                 // group has the same number of points, so the point loop is uniform) ----
@@ -612,9 +670,25 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                                 sL = NC;
                             }
                             const T *qR = temp + rs * nf * NC + cr;
-                            const T *pR_ = pr + rs * 5 * NC + cr;
-                            const T vkL = pL_[axis * sL], pLv = pL_[3 * sL], cL = pL_[4 * sL];
-                            const T vkR = pR_[axis * NC], pRv = pR_[3 * NC], cR = pR_[4 * NC];
+                            T vkL, pLv, cL, vkR, pRv, cR;
+                            if constexpr (SHARED_PRIMS) {
+                                const T *pR_ = pr + rs * 5 * NC + cr;
+                                vkL = pL_[axis * sL], pLv = pL_[3 * sL], cL = pL_[4 * sL];
+                                vkR = pR_[axis * NC], pRv = pR_[3 * NC], cR = pR_[4 * NC];
+                            } else {
+                                // primitives of both sides on the spot (cheap in FP32)
+                                T qh[6], v[3];
+#pragma unroll
+                                for (int f = 0; f < 6; f++)
+                                    qh[f] = qL[f * sL];
+                                prim_point(qh, gamma, gm1, ggm1, eps1, v, pLv, cL, bad);
+                                vkL = axis == 0 ? v[0] : (axis == 1 ? v[1] : v[2]);
+#pragma unroll
+                                for (int f = 0; f < 6; f++)
+                                    qh[f] = qR[f * NC];
+                                prim_point(qh, gamma, gm1, ggm1, eps1, v, pRv, cR, bad);
+                                vkR = axis == 0 ? v[0] : (axis == 1 ? v[1] : v[2]);
+                            }
                             const T a = max_nonneg(fabs(vkL) + cL, fabs(vkR) + cR);
                             amax = max_nonneg(amax, Num<T>::to_d(a));
                             // F_f = (F_f(L) + F_f(R))/2 - a (u_R - u_L)/2 written per side:
@@ -648,9 +722,11 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                             const int src = G.zp_src[z], dsts = G.zp_dst[z];
                             for (int f = 0; f < nf; f++)
                                 saved[(dsts * nf + f) * C64 + cl] = temp[(src * nf + f) * NC + cl];
+                            if constexpr (SHARED_PRIMS) {
 #pragma unroll
-                            for (int v = 0; v < 5; v++)
-                                prs[(dsts * 5 + v) * C64 + cl] = pr[(src * 5 + v) * NC + cl];
+                                for (int v = 0; v < 5; v++)
+                                    prs[(dsts * 5 + v) * C64 + cl] = pr[(src * 5 + v) * NC + cl];
+                            }
                         }
                     }
                 }
