@@ -9,7 +9,7 @@
 namespace octh {
 
 // precision: 0 FP64, 1 mixed; mode: 0 tile capacity 8x8 (one CTA per SM),
-// 1 capacity 8x4 (two CTAs per SM).
+// 1 capacity 8x4 (two CTAs per SM for FP64, three for the mixed form).
 size_t rhs_smem_bytes(int nf, int precision, int mode);
 bool build_group_tables(GroupTab *groups);
 cudaError_t rhs_prepare(int precision, int mode, int nf, int *ctas_per_sm);
