@@ -112,6 +112,10 @@ def _peaks():
 
 
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
+# DRAM bytes (read + write) of one launch of the FP64 RHS kernel on the
+# periodic 64^3 box, from the ncu capture summarised in
+# profiles/rhs_kernel_fp64_periodic_box_64.md; None once the kernel changes.
+RHS_FP64_TRAFFIC = {"periodic_box_64": 123494144 + 13161216}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
@@ -309,7 +313,8 @@ def run_ours(args, rank, world):
                                    "unit": "TFLOP/s", "frac": mx_tflops / FP32_PEAK_TFLOPS,
                                    "hbm_gbs": mx_gbs, "hbm_frac": mx_gbs / hbm_peak}},
         "roofline": {"bound": "alu", "achieved": rhs_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": rhs_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": rhs_tflops / FP64_PEAK_TFLOPS, "traffic": RHS_FP64_TRAFFIC.get(args.workload),
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "kernel": "rhs_kernel<double> (FP64 RHS)", "ops_per_cell": ops_cell,
                      "peak_source": "nominal FP64 of GB300 (1.25 TFLOP/s); a DFMA loop measured 1.0",
                      "hbm": {"achieved": rhs_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": rhs_gbs / hbm_peak,
