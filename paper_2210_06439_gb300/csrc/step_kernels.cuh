@@ -61,12 +61,32 @@ struct CombineArgs {
     unsigned *flags;
 };
 
+// e^(1/gamma).  For gamma = 5/3 (the ideal monatomic gas of every workload
+// here) y = e^(3/5) solves y^5 = e^3: an FP32 estimate refined by two Newton
+// steps y <- (4 y + e^3 / y^4) / 5 in FP64 (each step squares the relative
+// error; the FP32 start is good to about 1e-7).  Other gamma: pow.
+__device__ __forceinline__ double tau_of_eint(double e, double gamma)
+{
+    if (gamma == 5.0 / 3.0 && e > 1e-30 && e < 1e30) {
+        const float ef = (float)__double2float_rn(e);
+        double y = (double)__powf(ef, 0.6f);
+        const double e3 = e * e * e;
+        for (int it = 0; it < 2; it++) {
+            const double y2 = y * y;
+            y = (4.0 * y + e3 / (y2 * y2)) * 0.2;
+        }
+        return y;
+    }
+    return pow(e, 1.0 / gamma);
+}
+
 // One SSP-RK3 combine (Shu-Osher) on the interior, one block per subgrid:
 //   stage 1: out = X + dt L                     (X = U0)
 //   stage 2: out = 3/4 U0 + 1/4 (X + dt L)
 //   stage 3: out = 1/3 U0 + 2/3 (X + dt L)
 // then the floors rho >= rho_floor, rho_i >= 0, the tau re-synchronisation
 // tau = e_int^(1/gamma) where e_int = E - |s|^2/(2 rho) > eps2 E, and tau >= 0.
+// All loads of a cell are issued before its stores.
 __global__ void combine_kernel(CombineArgs A)
 {
     const int s = blockIdx.x;
@@ -85,19 +105,29 @@ __global__ void combine_kernel(CombineArgs A)
         a = 1.0 / 3.0;
         b = 2.0 / 3.0;
     }
+    const double *__restrict__ U0 = A.U0 + A.off[s];
+    const double *X = A.X + A.off[s];
+    const double *__restrict__ L = A.L + A.doff[s];
+    double *out = A.out + A.off[s];
     bool fired = false;
     for (int c = threadIdx.x; c < E3; c += blockDim.x) {
-        int x = c % E, y = (c / E) % E, z = c / (E * E);
-        long long gi = A.off[s] + ((long long)(z + NG) * B + (y + NG)) * B + (x + NG);
-        long long li = A.doff[s] + c;
+        const int x = c % E, y = (c / E) % E, z = c / (E * E);
+        const long long gi = ((long long)(z + NG) * B + (y + NG)) * B + (x + NG);
+        double xv[MAXNF], lv[MAXNF], u0[MAXNF];
+#pragma unroll
+        for (int f = 0; f < MAXNF; f++)
+            if (f < A.nf) {
+                xv[f] = X[gi + f * FS];
+                lv[f] = L[c + f * E3];
+                u0[f] = A.stage == 1 ? 0.0 : U0[gi + f * FS];
+            }
         double u[MAXNF];
 #pragma unroll
-        for (int f = 0; f < MAXNF; f++) {
+        for (int f = 0; f < MAXNF; f++)
             if (f < A.nf) {
-                double x1 = A.X[gi + f * FS] + dt * A.L[li + f * E3];
-                u[f] = (A.stage == 1) ? x1 : a * A.U0[gi + f * FS] + b * x1;
+                const double x1 = xv[f] + dt * lv[f];
+                u[f] = (A.stage == 1) ? x1 : a * u0[f] + b * x1;
             }
-        }
         if (u[F_RHO] < A.rho_floor) {
             u[F_RHO] = A.rho_floor;
             fired = true;
@@ -108,9 +138,9 @@ __global__ void combine_kernel(CombineArgs A)
                 u[f] = 0.0;
                 fired = true;
             }
-        double ei = u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) / u[F_RHO];
+        const double ei = u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) / u[F_RHO];
         if (ei > A.eps2 * u[F_EGAS])
-            u[F_TAU] = pow(ei, 1.0 / A.gamma);
+            u[F_TAU] = tau_of_eint(ei, A.gamma);
         if (u[F_TAU] < 0.0) {
             u[F_TAU] = 0.0;
             fired = true;
@@ -118,7 +148,7 @@ __global__ void combine_kernel(CombineArgs A)
 #pragma unroll
         for (int f = 0; f < MAXNF; f++)
             if (f < A.nf)
-                A.out[gi + f * FS] = u[f];
+                out[gi + f * FS] = u[f];
     }
     if (fired)
         atomicOr(A.flags, 2u);
@@ -134,17 +164,39 @@ __device__ __forceinline__ int nb_slot(int dx, int dy, int dz)
 // copies the matching interior cell of the neighbour subgrid; along an axis
 // whose face neighbour is missing (-1, a domain edge) the nearest interior
 // cell is copied instead (zero-gradient outflow).  Interiors are only read.
+// Ghost cells are enumerated directly (z slabs below and above the interior,
+// then y slabs, then x slabs of the remaining rows); a thread loads all fields
+// of its cell before storing them.
 __global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf, const int *nbr, unsigned *flags)
 {
     const int s = blockIdx.x;
     const int B = E + 2 * NG;
     const long long FS = (long long)B * B * B;
     const int *nb = nbr + 26 * (long long)s;
+    const int nzs = NG * B * B;   // cells of one z slab (3 planes)
+    const int nys = NG * B * E;   // one y slab within the interior z range
+    const int nxs = NG * E * E;   // one x slab within the interior y and z range
+    const int total = 2 * nzs + 2 * nys + 2 * nxs;
     bool err = false;
-    for (int c = threadIdx.x; c < B * B * B; c += blockDim.x) {
-        int g[3] = {c % B - NG, (c / B) % B - NG, c / (B * B) - NG};
-        if (g[0] >= 0 && g[0] < E && g[1] >= 0 && g[1] < E && g[2] >= 0 && g[2] < E)
-            continue;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        int g[3];
+        if (q < 2 * nzs) {
+            const int r = q % nzs, side = q / nzs;
+            g[0] = r % B - NG;
+            g[1] = (r / B) % B - NG;
+            g[2] = r / (B * B) + (side ? E : -NG);
+        } else if (q < 2 * nzs + 2 * nys) {
+            const int r0 = q - 2 * nzs, r = r0 % nys, side = r0 / nys;
+            g[0] = r % B - NG;
+            g[1] = (r / B) % NG + (side ? E : -NG);
+            g[2] = r / (B * NG);
+        } else {
+            const int r0 = q - 2 * nzs - 2 * nys, r = r0 % nxs, side = r0 / nxs;
+            g[0] = r % NG + (side ? E : -NG);
+            g[1] = (r / NG) % E;
+            g[2] = r / (NG * E);
+        }
+        const long long di = off[s] + ((long long)(g[2] + NG) * B + (g[1] + NG)) * B + (g[0] + NG);
         int d[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
@@ -166,11 +218,17 @@ __global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf
                 continue;
             }
         }
-        long long si = off[src] + ((long long)(g[2] - d[2] * E + NG) * B + (g[1] - d[1] * E + NG)) * B +
-                       (g[0] - d[0] * E + NG);
-        long long di = off[s] + c;
-        for (int f = 0; f < nf; f++)
-            U[di + f * FS] = U[si + f * FS];
+        const long long si = off[src] + ((long long)(g[2] - d[2] * E + NG) * B + (g[1] - d[1] * E + NG)) * B +
+                             (g[0] - d[0] * E + NG);
+        double v[MAXNF];
+#pragma unroll
+        for (int f = 0; f < MAXNF; f++)
+            if (f < nf)
+                v[f] = U[si + f * FS];
+#pragma unroll
+        for (int f = 0; f < MAXNF; f++)
+            if (f < nf)
+                U[di + f * FS] = v[f];
     }
     if (err)
         atomicOr(flags, 4u);
