@@ -63,12 +63,13 @@ struct oct_hydro {
     std::vector<int> nbr;
     std::vector<WorkItem> items;
     std::vector<int> item_begin;
+    std::vector<long long> cell_begin;  // packed interior-cell offset of each subgrid
     long long state_len = 0, rhs_len = 0;
     int tile_mode = 0;       // 0: 8x8 tiles (6x6 for edge 12); 1: 8x4 tiles (6x4 for edge 12)
     int ctas_per_sm[2][2] = {{0, 0}, {0, 0}};  // [precision][tile mode]
     // device memory
     int *d_edge = nullptr, *d_nbr = nullptr, *d_item_begin = nullptr;
-    long long *d_off = nullptr, *d_doff = nullptr;
+    long long *d_off = nullptr, *d_doff = nullptr, *d_cell_begin = nullptr;
     double *d_dx = nullptr;
     WorkItem *d_items = nullptr;
     double *d_amax_tile = nullptr, *d_dt = nullptr, *d_W = nullptr, *d_L = nullptr, *d_Uhost = nullptr,
@@ -100,6 +101,7 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_item_begin);
     dfree(h->d_off);
     dfree(h->d_doff);
+    dfree(h->d_cell_begin);
     dfree(h->d_dx);
     dfree(h->d_items);
     dfree(h->d_amax_tile);
@@ -302,6 +304,11 @@ extern "C" oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, 
     CUDA_TRY(cudaMemcpy(h->d_off, off.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&h->d_doff, sizeof(long long) * n));
     CUDA_TRY(cudaMemcpy(h->d_doff, doff.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
+    h->cell_begin.resize(n);
+    for (int s = 0; s < n; s++)
+        h->cell_begin[s] = doff[s] / nf;
+    CUDA_TRY(cudaMalloc(&h->d_cell_begin, sizeof(long long) * n));
+    CUDA_TRY(cudaMemcpy(h->d_cell_begin, h->cell_begin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
     if (!nb.empty()) {
         CUDA_TRY(cudaMalloc(&h->d_nbr, sizeof(int) * nb.size()));
         CUDA_TRY(cudaMemcpy(h->d_nbr, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice));
@@ -498,7 +505,8 @@ static oct_status launch_combine(oct_hydro *h, int stage, const double *U0, cons
     A.rho_floor = h->rho_floor;
     A.eps2 = h->eps2;
     A.flags = h->d_flags;
-    combine_kernel<<<h->n_sub, 256, 0, s>>>(A);
+    const long long n_cells = h->rhs_len / h->nf;
+    combine_kernel<<<(unsigned)((n_cells + 255) / 256), 256, 0, s>>>(A, h->n_sub, h->d_cell_begin, n_cells);
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;
 }

@@ -80,19 +80,33 @@ __device__ __forceinline__ double tau_of_eint(double e, double gamma)
     return pow(e, 1.0 / gamma);
 }
 
-// One SSP-RK3 combine (Shu-Osher) on the interior, one block per subgrid:
+// One SSP-RK3 combine (Shu-Osher) on the interior, one thread per interior
+// cell of the whole batch (cell q of subgrid s at q - cell_begin[s]):
 //   stage 1: out = X + dt L                     (X = U0)
 //   stage 2: out = 3/4 U0 + 1/4 (X + dt L)
 //   stage 3: out = 1/3 U0 + 2/3 (X + dt L)
 // then the floors rho >= rho_floor, rho_i >= 0, the tau re-synchronisation
 // tau = e_int^(1/gamma) where e_int = E - |s|^2/(2 rho) > eps2 E, and tau >= 0.
 // All loads of a cell are issued before its stores.
-__global__ void combine_kernel(CombineArgs A)
+__global__ void combine_kernel(CombineArgs A, int n_sub, const long long *cell_begin, long long n_cells)
 {
-    const int s = blockIdx.x;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_cells)
+        return;
+    // subgrid of this cell: binary search over the packed cell offsets
+    int lo = 0, hi = n_sub - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cell_begin[mid] <= q)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int s = lo;
     const int E = A.edge[s], B = E + 2 * NG;
     const long long FS = (long long)B * B * B;
     const long long E3 = (long long)E * E * E;
+    const int c = (int)(q - cell_begin[s]);
     const double dt = A.dt[0];
     double a, b;
     if (A.stage == 1) {
@@ -105,51 +119,46 @@ __global__ void combine_kernel(CombineArgs A)
         a = 1.0 / 3.0;
         b = 2.0 / 3.0;
     }
-    const double *__restrict__ U0 = A.U0 + A.off[s];
-    const double *X = A.X + A.off[s];
-    const double *__restrict__ L = A.L + A.doff[s];
-    double *out = A.out + A.off[s];
+    const int x = c % E, y = (c / E) % E, z = c / (E * E);
+    const long long gi = A.off[s] + ((long long)(z + NG) * B + (y + NG)) * B + (x + NG);
+    const long long li = A.doff[s] + c;
+    double xv[MAXNF], lv[MAXNF], u0[MAXNF];
+#pragma unroll
+    for (int f = 0; f < MAXNF; f++)
+        if (f < A.nf) {
+            xv[f] = A.X[gi + f * FS];
+            lv[f] = A.L[li + f * E3];
+            u0[f] = A.stage == 1 ? 0.0 : A.U0[gi + f * FS];
+        }
+    double u[MAXNF];
+#pragma unroll
+    for (int f = 0; f < MAXNF; f++)
+        if (f < A.nf) {
+            const double x1 = xv[f] + dt * lv[f];
+            u[f] = (A.stage == 1) ? x1 : a * u0[f] + b * x1;
+        }
     bool fired = false;
-    for (int c = threadIdx.x; c < E3; c += blockDim.x) {
-        const int x = c % E, y = (c / E) % E, z = c / (E * E);
-        const long long gi = ((long long)(z + NG) * B + (y + NG)) * B + (x + NG);
-        double xv[MAXNF], lv[MAXNF], u0[MAXNF];
-#pragma unroll
-        for (int f = 0; f < MAXNF; f++)
-            if (f < A.nf) {
-                xv[f] = X[gi + f * FS];
-                lv[f] = L[c + f * E3];
-                u0[f] = A.stage == 1 ? 0.0 : U0[gi + f * FS];
-            }
-        double u[MAXNF];
-#pragma unroll
-        for (int f = 0; f < MAXNF; f++)
-            if (f < A.nf) {
-                const double x1 = xv[f] + dt * lv[f];
-                u[f] = (A.stage == 1) ? x1 : a * u0[f] + b * x1;
-            }
-        if (u[F_RHO] < A.rho_floor) {
-            u[F_RHO] = A.rho_floor;
-            fired = true;
-        }
-#pragma unroll
-        for (int f = F_SPC; f < MAXNF; f++)
-            if (f < A.nf && u[f] < 0.0) {
-                u[f] = 0.0;
-                fired = true;
-            }
-        const double ei = u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) / u[F_RHO];
-        if (ei > A.eps2 * u[F_EGAS])
-            u[F_TAU] = tau_of_eint(ei, A.gamma);
-        if (u[F_TAU] < 0.0) {
-            u[F_TAU] = 0.0;
-            fired = true;
-        }
-#pragma unroll
-        for (int f = 0; f < MAXNF; f++)
-            if (f < A.nf)
-                out[gi + f * FS] = u[f];
+    if (u[F_RHO] < A.rho_floor) {
+        u[F_RHO] = A.rho_floor;
+        fired = true;
     }
+#pragma unroll
+    for (int f = F_SPC; f < MAXNF; f++)
+        if (f < A.nf && u[f] < 0.0) {
+            u[f] = 0.0;
+            fired = true;
+        }
+    const double ei = u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) / u[F_RHO];
+    if (ei > A.eps2 * u[F_EGAS])
+        u[F_TAU] = tau_of_eint(ei, A.gamma);
+    if (u[F_TAU] < 0.0) {
+        u[F_TAU] = 0.0;
+        fired = true;
+    }
+#pragma unroll
+    for (int f = 0; f < MAXNF; f++)
+        if (f < A.nf)
+            A.out[gi + f * FS] = u[f];
     if (fired)
         atomicOr(A.flags, 2u);
 }

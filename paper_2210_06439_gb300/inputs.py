@@ -422,3 +422,22 @@ WORKLOADS = {
     "binary_star_128": lambda: binary_star(16),
     "binary_star_256": lambda: binary_star(32),
 }
+
+
+def sedov_blast(nsub: int = 8, E: int = 8, e_blast: float = 1.0, rho0: float = 1.0, p_amb: float = 1e-5,
+                r_dep_cells: float = 2.0) -> Problem:
+    """Sedov-Taylor point explosion (the paper's hydro-only test scenario,
+    Sec. V-C): a uniform cold gas rho0, p_amb at rest in the unit box (outflow
+    edges), with energy e_blast deposited as thermal energy, evenly, in the
+    cells whose centres lie within r_dep_cells cells of the box centre."""
+    N = nsub * E
+    c = (np.arange(N) + 0.5) / N
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt((xx - 0.5) ** 2 + (yy - 0.5) ** 2 + (zz - 0.5) ** 2)
+    hot = r < r_dep_cells / N
+    vol = hot.sum() / N ** 3
+    p = np.where(hot, (GAMMA - 1.0) * e_blast / vol, p_amb)
+    z = np.zeros_like(r)
+    fields = conserved(np.full_like(r, rho0), z, z, z, p, [np.where(hot, rho0, 0.0)])
+    return _tile_global(f"sedov_{N}", fields, (nsub,) * 3, E, 1.0 / N, 2, False,
+                        meta=dict(e_blast=e_blast, rho0=rho0))
