@@ -62,41 +62,6 @@ constexpr long long EXP1 = 1LL << 52;
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(long long b) { return __longlong_as_double(b); }
 
-// double -> float for operands known to be in the normal float range,
-// truncating the mantissa (an estimate only); returns false otherwise.
-__device__ __forceinline__ bool d2f_est(double x, float &f)
-{
-    long long b = dbits(x);
-    int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
-    unsigned int m = (unsigned int)((b >> 29) & 0x7FFFFF);
-    f = __uint_as_float(((unsigned int)(b >> 32) & 0x80000000u) | ((unsigned int)e << 23) | m);
-    return e > 1 && e < 253;
-}
-
-__device__ __forceinline__ double f2d_normal(float f)
-{
-    unsigned int b = __float_as_uint(f);
-    unsigned long long e = ((b >> 23) & 0xFF) - 127 + 1023;
-    return bitsd((long long)(((unsigned long long)(b & 0x80000000u) << 32) | (e << 52) |
-                             ((unsigned long long)(b & 0x7FFFFF) << 29)));
-}
-
-// 1/x: FP32 reciprocal estimate (rcp.approx, about 2^-22 relative), then two
-// Newton-Raphson steps r <- r + r (1 - x r), each squaring the relative error.
-__device__ __forceinline__ double rcp_nr(double x)
-{
-    float xf;
-    if (!d2f_est(x, xf))
-        return 1.0 / x;
-    float rf;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
-    double r = f2d_normal(rf);
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
-}
-
 // sqrt(q): FP32 reciprocal-square-root estimate y (about 2^-22), s = q y,
 // then two Newton (Heron) corrections s <- s + (q - s^2) y / 2.
 __device__ __forceinline__ double sqrt_nr(double q)

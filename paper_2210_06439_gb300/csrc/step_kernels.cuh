@@ -62,20 +62,16 @@ struct CombineArgs {
 };
 
 // e^(1/gamma).  For gamma = 5/3 (the ideal monatomic gas of every workload
-// here) y = e^(3/5) solves y^5 = e^3: an FP32 estimate refined by two Newton
-// steps y <- (4 y + e^3 / y^4) / 5 in FP64 (each step squares the relative
-// error; the FP32 start is good to about 1e-7).  Other gamma: pow.
+// here) y = e^(3/5) solves y^5 = e^3: an FP32 estimate (powf, about 1e-7)
+// refined by one Newton step y <- (4 y + e^3 / y^4) / 5 in FP64, which
+// squares the relative error (about 1e-14 after it).  Other gamma: pow.
 __device__ __forceinline__ double tau_of_eint(double e, double gamma)
 {
-    if (gamma == 5.0 / 3.0 && e > 1e-30 && e < 1e30) {
-        const float ef = (float)__double2float_rn(e);
-        double y = (double)__powf(ef, 0.6f);
-        const double e3 = e * e * e;
-        for (int it = 0; it < 2; it++) {
-            const double y2 = y * y;
-            y = (4.0 * y + e3 / (y2 * y2)) * 0.2;
-        }
-        return y;
+    float ef;
+    if (gamma == 5.0 / 3.0 && d2f_est(e, ef)) {
+        const double y = f2d_normal(powf(ef, 0.6f));
+        const double y2 = y * y;
+        return fma(4.0, y, e * e * e * rcp_nr(y2 * y2)) * 0.2;
     }
     return pow(e, 1.0 / gamma);
 }
@@ -144,11 +140,15 @@ __global__ void combine_kernel(CombineArgs A, int n_sub, const long long *cell_b
     }
 #pragma unroll
     for (int f = F_SPC; f < MAXNF; f++)
-        if (f < A.nf && u[f] < 0.0) {
-            u[f] = 0.0;
-            fired = true;
+        if (f < A.nf) {
+            const int hi = __double2hiint(u[f]);
+            if (hi < 0 && ((hi & 0x7FFFFFFF) | __double2loint(u[f])) != 0) {  // negative, not -0
+                u[f] = 0.0;
+                fired = true;
+            }
         }
-    const double ei = u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) / u[F_RHO];
+    const double ei =
+        u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) * rcp_nr(u[F_RHO]);
     if (ei > A.eps2 * u[F_EGAS])
         u[F_TAU] = tau_of_eint(ei, A.gamma);
     if (u[F_TAU] < 0.0) {
