@@ -77,7 +77,7 @@ typedef enum {
 
 typedef enum { OCT_FP64 = 0, OCT_MIXED = 1 } oct_precision;
 
-typedef enum { OCT_BC_GIVEN = 0, OCT_BC_PERIODIC = 1, OCT_BC_OUTFLOW = 2 } oct_bc;
+typedef enum { OCT_BC_GIVEN = 0, OCT_BC_PERIODIC = 1, OCT_BC_OUTFLOW = 2, OCT_BC_AMR = 3 } oct_bc;
 
 /* Device error flags (oct_hydro_get_error_flags). */
 #define OCT_FLAG_NONPHYS 0x1u /* rho <= 0 or non-finite value at a point   */
@@ -109,6 +109,21 @@ oct_status oct_hydro_create(int n_subgrids, int edge, int ghost, int n_species, 
 oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, const int64_t *offsets, const double *dx,
                                 const int32_t *level, const int32_t *neighbours, int bc);
 
+/* Ghost exchange across refinement levels (Sec. II "Data-Structure": an
+ * adaptive octree with one subgrid per leaf).  All subgrids share one even
+ * edge E; subgrid s sits at level level[s] >= 0 and covers the cells
+ * origin[3s..3s+2] .. +E-1 of its level (HOST arrays, origins multiples of E),
+ * in a root box of root_cells cells per side at level 0 (root_cells * 2^l at
+ * level l), periodic (periodic != 0) or with outflow edges.  Each ghost cell
+ * then takes: the covering cell of a subgrid at the same level (a copy); else
+ * the covering cell one level coarser (prolongation by injection); else the
+ * mean of the 8 cells one level finer (restriction).  No flux correction is
+ * applied at coarse-fine faces.  Sets the boundary mode to OCT_BC_AMR (used
+ * by oct_hydro_fill_ghosts and oct_hydro_rk_step); OCT_E_ARG when a ghost
+ * cell has no source (levels not properly nested) or the arrays are invalid. */
+oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, const int32_t *origin, int root_cells,
+                             int periodic);
+
 /* Numerical parameters: precision (oct_precision: FP64 everywhere, or
  * reconstruction/flux arithmetic in FP32 with FP64 divergence, update,
  * floors and dt), CFL number (0 < cfl <= 1, default 0.4), density floor
@@ -137,8 +152,9 @@ oct_status oct_hydro_rhs(oct_hydro_t h, const double *U, double *dUdt, double *a
  * synchronises the stream. */
 oct_status oct_hydro_max_dt(oct_hydro_t h, const double *U, double *dt_host_out, void *cuda_stream);
 
-/* Fills the ghost layers of U on a uniform level from the neighbour table
- * (periodic or outflow); does nothing for OCT_BC_GIVEN. */
+/* Fills the ghost layers of U: on a uniform level from the neighbour table
+ * (periodic or outflow), across levels after oct_hydro_set_amr; does
+ * nothing for OCT_BC_GIVEN. */
 oct_status oct_hydro_fill_ghosts(oct_hydro_t h, double *U, void *cuda_stream);
 
 /* One SSP-RK3 time step in place (three hydro iterations per time step,

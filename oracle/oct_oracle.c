@@ -39,7 +39,11 @@
  *       dt = cfl * min over subgrids of dx / a_max;
  *   R9  ghost fill on a uniform level: copy from the neighbour subgrid's
  *       interior; at a domain edge with no neighbour, copy the nearest
- *       interior cell (zero-gradient outflow).
+ *       interior cell (zero-gradient outflow);
+ *   R14 ghost fill across refinement levels: the same-level cell if one
+ *       covers the ghost, else the covering coarser cell (injection), else
+ *       the mean of the 8 finer cells (restriction); no flux correction at
+ *       coarse-fine faces.
  *
  * Field order: rho, s_x, s_y, s_z, E_gas, tau, rho_1 .. rho_ns.
  * State layout: one ghosted block per subgrid, structure of arrays
@@ -601,9 +605,44 @@ int oco_rk_combine(int stage, int n_sub, const int32_t *edge, const int64_t *off
  * expressed by nbr).  On entry U's ghosts must be valid.  *dt_out receives
  * the dt used; *floors_out (may be NULL) the number of floor firings.
  * Returns 0, 1 if a non-physical state was met, or a negative error. */
+int oco_amr_ghost_fill(int n_sub, int E, const int64_t *off, int nf, const int32_t *lev, const int32_t *org,
+                       int n0, int periodic, double *U);
+
+/* amr (may be NULL): when bc == 3, the ghosts are refreshed by the ghost
+ * fill across levels with amr->lev, amr->org, amr->n0, amr->periodic. */
+typedef struct {
+    const int32_t *lev, *org;
+    int n0, periodic;
+} oco_amr;
+
+static int rk3_step_impl(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
+                         double eps1, double eps2, double rho_floor, double cfl, double dt_cap, int bc,
+                         const int32_t *nbr, const oco_amr *amr, double *U, int64_t total_len, double *dt_out,
+                         int64_t *floors_out, int nthreads);
+
 int oco_rk3_step(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
                  double eps1, double eps2, double rho_floor, double cfl, double dt_cap, int bc, const int32_t *nbr,
                  double *U, int64_t total_len, double *dt_out, int64_t *floors_out, int nthreads)
+{
+    return rk3_step_impl(n_sub, edge, off, dx, nf, gamma, eps1, eps2, rho_floor, cfl, dt_cap, bc, nbr, NULL, U,
+                         total_len, dt_out, floors_out, nthreads);
+}
+
+/* One SSP-RK3 step with the ghost fill across refinement levels (reading R14). */
+int oco_rk3_step_amr(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
+                     double eps1, double eps2, double rho_floor, double cfl, double dt_cap, const int32_t *lev,
+                     const int32_t *org, int n0, int periodic, double *U, int64_t total_len, double *dt_out,
+                     int64_t *floors_out, int nthreads)
+{
+    oco_amr a = {lev, org, n0, periodic};
+    return rk3_step_impl(n_sub, edge, off, dx, nf, gamma, eps1, eps2, rho_floor, cfl, dt_cap, 3, NULL, &a, U,
+                         total_len, dt_out, floors_out, nthreads);
+}
+
+static int rk3_step_impl(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
+                         double eps1, double eps2, double rho_floor, double cfl, double dt_cap, int bc,
+                         const int32_t *nbr, const oco_amr *amr, double *U, int64_t total_len, double *dt_out,
+                         int64_t *floors_out, int nthreads)
 {
     if (n_sub <= 0)
         return -1;
@@ -635,7 +674,12 @@ int oco_rk3_step(int n_sub, const int32_t *edge, const int64_t *off, const doubl
         }
         oco_rk_combine(stage, n_sub, edge, off, nf, dt, U0, L, U);
         fired += oco_floors(n_sub, edge, off, nf, gamma, rho_floor, eps2, U);
-        if (bc != 0 && oco_ghost_fill(n_sub, edge[0], off, nf, nbr, U) != 0) {
+        if (bc == 3) {
+            if (oco_amr_ghost_fill(n_sub, edge[0], off, nf, amr->lev, amr->org, amr->n0, amr->periodic, U) != 0) {
+                bad = -2;
+                break;
+            }
+        } else if (bc != 0 && oco_ghost_fill(n_sub, edge[0], off, nf, nbr, U) != 0) {
             bad = -2;
             break;
         }
@@ -647,4 +691,112 @@ int oco_rk3_step(int n_sub, const int32_t *edge, const int64_t *off, const doubl
     if (floors_out)
         *floors_out = fired;
     return bad;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ghost fill across refinement levels (reading R14)                         */
+/* ------------------------------------------------------------------------ */
+
+/* Subgrids of a common edge E sit on an octree-like set of levels: subgrid s
+ * at level lev[s] covers the cells org[3s..3s+2] .. +E-1 of its level, in a
+ * root box of n0 cells per side at level 0 (n0 * 2^l cells at level l);
+ * periodic != 0 wraps the root box, else its edges are outflow (zero
+ * gradient).  Each ghost cell takes, by geometric search:
+ *   - the cell of a subgrid at the same level that covers it (a copy);
+ *   - else the covering cell one level coarser (prolongation by injection:
+ *     the fine ghost takes the coarse cell's value);
+ *   - else the mean of the 8 cells one level finer that cover it
+ *     (restriction).
+ * At an outflow edge the ghost cell's position is first clamped into the
+ * root box.  Returns 0, or -2 when some ghost cell has no source. */
+static int find_cover(int n_sub, int E, const int32_t *lev, const int32_t *org, int l, const int64_t *c)
+{
+    for (int s = 0; s < n_sub; s++) {
+        if (lev[s] != l)
+            continue;
+        int in = 1;
+        for (int a = 0; a < 3; a++)
+            if (c[a] < org[3 * s + a] || c[a] >= org[3 * s + a] + E)
+                in = 0;
+        if (in)
+            return s;
+    }
+    return -1;
+}
+
+int oco_amr_ghost_fill(int n_sub, int E, const int64_t *off, int nf, const int32_t *lev, const int32_t *org,
+                       int n0, int periodic, double *U)
+{
+    if (!valid_edge(E))
+        return -1;
+    int B = E + 2 * NG;
+    int64_t fs = (int64_t)B * B * B;
+    int err = 0;
+    for (int s = 0; s < n_sub; s++) {
+        int l = lev[s];
+        int64_t nl = (int64_t)n0 << l; /* cells per side at this level */
+        for (int z = -NG; z < E + NG; z++)
+            for (int y = -NG; y < E + NG; y++)
+                for (int x = -NG; x < E + NG; x++) {
+                    if (x >= 0 && x < E && y >= 0 && y < E && z >= 0 && z < E)
+                        continue;
+                    int64_t g[3] = {org[3 * s] + x, org[3 * s + 1] + y, org[3 * s + 2] + z};
+                    for (int a = 0; a < 3; a++) {
+                        if (periodic)
+                            g[a] = ((g[a] % nl) + nl) % nl;
+                        else
+                            g[a] = g[a] < 0 ? 0 : (g[a] >= nl ? nl - 1 : g[a]);
+                    }
+                    int64_t dst = off[s] + cidx(B, x + NG, y + NG, z + NG);
+                    /* same level */
+                    int t = find_cover(n_sub, E, lev, org, l, g);
+                    if (t >= 0) {
+                        int64_t src = off[t] + cidx(B, (int)(g[0] - org[3 * t]) + NG, (int)(g[1] - org[3 * t + 1]) + NG,
+                                                    (int)(g[2] - org[3 * t + 2]) + NG);
+                        for (int f = 0; f < nf; f++)
+                            U[dst + f * fs] = U[src + f * fs];
+                        continue;
+                    }
+                    /* one level coarser: the coarse cell containing this one */
+                    if (l > 0) {
+                        int64_t gc[3] = {g[0] >> 1, g[1] >> 1, g[2] >> 1};
+                        t = find_cover(n_sub, E, lev, org, l - 1, gc);
+                        if (t >= 0) {
+                            int64_t src = off[t] + cidx(B, (int)(gc[0] - org[3 * t]) + NG,
+                                                        (int)(gc[1] - org[3 * t + 1]) + NG,
+                                                        (int)(gc[2] - org[3 * t + 2]) + NG);
+                            for (int f = 0; f < nf; f++)
+                                U[dst + f * fs] = U[src + f * fs];
+                            continue;
+                        }
+                    }
+                    /* one level finer: mean of the 8 children */
+                    {
+                        int64_t gf[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
+                        t = find_cover(n_sub, E, lev, org, l + 1, gf);
+                        if (t < 0) {
+                            err = 1;
+                            continue;
+                        }
+                        for (int f = 0; f < nf; f++) {
+                            double sum = 0.0;
+                            for (int dz = 0; dz < 2; dz++)
+                                for (int dy = 0; dy < 2; dy++)
+                                    for (int dx = 0; dx < 2; dx++) {
+                                        int64_t ch[3] = {gf[0] + dx, gf[1] + dy, gf[2] + dz};
+                                        int u = find_cover(n_sub, E, lev, org, l + 1, ch);
+                                        if (u < 0) {
+                                            err = 1;
+                                            continue;
+                                        }
+                                        sum += U[off[u] + f * fs +
+                                                 cidx(B, (int)(ch[0] - org[3 * u]) + NG, (int)(ch[1] - org[3 * u + 1]) + NG,
+                                                      (int)(ch[2] - org[3 * u + 2]) + NG)];
+                                    }
+                            U[dst + f * fs] = sum / 8.0;
+                        }
+                    }
+                }
+    }
+    return err ? -2 : 0;
 }

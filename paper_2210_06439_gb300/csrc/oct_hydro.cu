@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -75,6 +76,7 @@ struct oct_hydro {
     double *d_amax_tile = nullptr, *d_dt = nullptr, *d_W = nullptr, *d_L = nullptr, *d_Uhost = nullptr,
            *d_Lhost = nullptr;
     unsigned *d_flags = nullptr;
+    int2 *d_amr_plan = nullptr;  // ghost-cell sources across levels (OCT_BC_AMR)
     std::map<const double *, GraphEntry> graphs;
 };
 
@@ -109,6 +111,7 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_L);
     dfree(h->d_Uhost);
     dfree(h->d_Lhost);
+    dfree(h->d_amr_plan);
     drop_graphs(h);
 }
 
@@ -320,6 +323,108 @@ extern "C" oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, 
     return OCT_OK;
 }
 
+extern "C" oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, const int32_t *origin, int root_cells,
+                                        int periodic)
+{
+    if (!h)
+        return fail(OCT_E_ARG, "handle is NULL");
+    if (!h->layout_ok)
+        return fail(OCT_E_STATE, "no layout set");
+    if (!level || !origin)
+        return fail(OCT_E_ARG, "level and origin are required");
+    const int n = h->n_sub, E = h->edge[0];
+    for (int s = 0; s < n; s++)
+        if (h->edge[s] != E)
+            return fail(OCT_E_ARG, "ghost exchange needs one common edge");
+    if (E % 2 != 0)
+        return fail(OCT_E_ARG, "ghost exchange across levels needs an even edge (got %d)", E);
+    if (root_cells <= 0 || root_cells % E != 0)
+        return fail(OCT_E_ARG, "root_cells must be a positive multiple of the edge (got %d)", root_cells);
+    // subgrid lookup by (level, subgrid coordinates)
+    auto key = [](long long l, long long a, long long b, long long c) {
+        return (((l * 4096 + a) * 4096 + b) * 4096) + c;
+    };
+    std::unordered_map<long long, int> at;
+    for (int s = 0; s < n; s++) {
+        const int l = level[s];
+        if (l < 0 || l > 20)
+            return fail(OCT_E_ARG, "level of subgrid %d out of range (%d)", s, l);
+        const long long nl = (long long)root_cells << l;
+        for (int a = 0; a < 3; a++)
+            if (origin[3 * s + a] < 0 || origin[3 * s + a] % E != 0 || origin[3 * s + a] + E > nl)
+                return fail(OCT_E_ARG, "origin of subgrid %d must be a multiple of %d inside its level", s, E);
+        if (nl / E >= 4096)
+            return fail(OCT_E_ARG, "too many subgrids per side at level %d", l);
+        auto ins = at.emplace(key(l, origin[3 * s] / E, origin[3 * s + 1] / E, origin[3 * s + 2] / E), s);
+        if (!ins.second)
+            return fail(OCT_E_ARG, "subgrids %d and %d overlap", ins.first->second, s);
+    }
+    auto cover = [&](int l, const long long *c) -> int {
+        if (l < 0)
+            return -1;
+        auto it = at.find(key(l, c[0] / E, c[1] / E, c[2] / E));
+        return it == at.end() ? -1 : it->second;
+    };
+    const int B = E + 2 * NG;
+    const int nzs = NG * B * B, nys = NG * B * E, nxs = NG * E * E;
+    const int G = 2 * nzs + 2 * nys + 2 * nxs;
+    std::vector<int2> plan((size_t)n * G);
+    for (int s = 0; s < n; s++) {
+        const int l = level[s];
+        const long long nl = (long long)root_cells << l;
+        for (int q = 0; q < G; q++) {
+            int g[3];  // the enumeration of amr_ghost_kernel
+            if (q < 2 * nzs) {
+                const int r = q % nzs, side = q / nzs;
+                g[0] = r % B - NG;
+                g[1] = (r / B) % B - NG;
+                g[2] = r / (B * B) + (side ? E : -NG);
+            } else if (q < 2 * nzs + 2 * nys) {
+                const int r0 = q - 2 * nzs, r = r0 % nys, side = r0 / nys;
+                g[0] = r % B - NG;
+                g[1] = (r / B) % NG + (side ? E : -NG);
+                g[2] = r / (B * NG);
+            } else {
+                const int r0 = q - 2 * nzs - 2 * nys, r = r0 % nxs, side = r0 / nxs;
+                g[0] = r % NG + (side ? E : -NG);
+                g[1] = (r / NG) % E;
+                g[2] = r / (NG * E);
+            }
+            long long c[3];
+            for (int a = 0; a < 3; a++) {
+                c[a] = (long long)origin[3 * s + a] + g[a];
+                c[a] = periodic ? ((c[a] % nl) + nl) % nl : (c[a] < 0 ? 0 : (c[a] >= nl ? nl - 1 : c[a]));
+            }
+            auto local = [&](int t, const long long *p) {
+                return ((p[2] - origin[3 * t + 2] + NG) * B + (p[1] - origin[3 * t + 1] + NG)) * B +
+                       (p[0] - origin[3 * t] + NG);
+            };
+            int t = cover(l, c);
+            if (t >= 0) {
+                plan[(size_t)s * G + q] = make_int2(t, (int)local(t, c));
+                continue;
+            }
+            const long long cc[3] = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
+            t = cover(l - 1, cc);
+            if (t >= 0) {
+                plan[(size_t)s * G + q] = make_int2(t, (int)local(t, cc));
+                continue;
+            }
+            const long long cf[3] = {2 * c[0], 2 * c[1], 2 * c[2]};
+            t = cover(l + 1, cf);
+            if (t < 0)
+                return fail(OCT_E_ARG, "ghost cell %d of subgrid %d has no source (levels not properly nested)", q, s);
+            plan[(size_t)s * G + q] = make_int2((int)(t | 0x80000000u), (int)local(t, cf));
+        }
+    }
+    dfree(h->d_amr_plan);
+    CUDA_TRY(cudaMalloc(&h->d_amr_plan, sizeof(int2) * plan.size()));
+    CUDA_TRY(cudaMemcpy(h->d_amr_plan, plan.data(), sizeof(int2) * plan.size(), cudaMemcpyHostToDevice));
+    h->bc = OCT_BC_AMR;
+    drop_graphs(h);
+    return OCT_OK;
+}
+
 extern "C" oct_status oct_hydro_set_params(oct_hydro_t h, int precision, double cfl, double rho_floor,
                                            double de_switch1, double de_switch2)
 {
@@ -472,6 +577,11 @@ static oct_status launch_ghosts(oct_hydro *h, double *U, cudaStream_t s)
 {
     if (h->bc == OCT_BC_GIVEN)
         return OCT_OK;
+    if (h->bc == OCT_BC_AMR) {
+        amr_ghost_kernel<<<h->n_sub, 256, 0, s>>>(U, h->edge[0], h->d_off, h->nf, h->d_amr_plan, h->d_flags);
+        CUDA_TRY(cudaGetLastError());
+        return OCT_OK;
+    }
     ghost_fill_kernel<<<h->n_sub, 256, 0, s>>>(U, h->edge[0], h->d_off, h->nf, h->d_nbr, h->d_flags);
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;

@@ -243,4 +243,66 @@ __global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf
         atomicOr(flags, 4u);
 }
 
+// Ghost fill across refinement levels from a host-built plan: entry q of
+// subgrid s (ghost cells enumerated as in ghost_fill_kernel) holds the source
+// subgrid (bit 31 set: the mean of the 2x2x2 cells starting there,
+// otherwise a copy) and the source cell's index in its ghosted block.
+// Interiors are only read; the 8 cells of a mean are summed in z, y, x order.
+__global__ void amr_ghost_kernel(double *U, int E, const long long *off, int nf, const int2 *plan, unsigned *flags)
+{
+    const int s = blockIdx.x;
+    const int B = E + 2 * NG;
+    const long long FS = (long long)B * B * B;
+    const int nzs = NG * B * B, nys = NG * B * E, nxs = NG * E * E;
+    const int total = 2 * nzs + 2 * nys + 2 * nxs;
+    const int2 *pl = plan + (long long)s * total;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        int g[3];
+        if (q < 2 * nzs) {
+            const int r = q % nzs, side = q / nzs;
+            g[0] = r % B - NG;
+            g[1] = (r / B) % B - NG;
+            g[2] = r / (B * B) + (side ? E : -NG);
+        } else if (q < 2 * nzs + 2 * nys) {
+            const int r0 = q - 2 * nzs, r = r0 % nys, side = r0 / nys;
+            g[0] = r % B - NG;
+            g[1] = (r / B) % NG + (side ? E : -NG);
+            g[2] = r / (B * NG);
+        } else {
+            const int r0 = q - 2 * nzs - 2 * nys, r = r0 % nxs, side = r0 / nxs;
+            g[0] = r % NG + (side ? E : -NG);
+            g[1] = (r / NG) % E;
+            g[2] = r / (NG * E);
+        }
+        const long long di = off[s] + ((long long)(g[2] + NG) * B + (g[1] + NG)) * B + (g[0] + NG);
+        const int2 e = pl[q];
+        const int t = e.x & 0x7FFFFFFF;
+        const long long si = off[t] + e.y;
+        double v[MAXNF];
+        if (e.x < 0) {
+#pragma unroll
+            for (int f = 0; f < MAXNF; f++)
+                if (f < nf) {
+                    const double *c = U + si + f * FS;
+                    double sum = 0.0;
+                    for (int dz = 0; dz < 2; dz++)
+                        for (int dy = 0; dy < 2; dy++)
+                            for (int dx = 0; dx < 2; dx++)
+                                sum += c[(long long)dz * B * B + dy * B + dx];
+                    v[f] = sum / 8.0;
+                }
+        } else {
+#pragma unroll
+            for (int f = 0; f < MAXNF; f++)
+                if (f < nf)
+                    v[f] = U[si + f * FS];
+        }
+#pragma unroll
+        for (int f = 0; f < MAXNF; f++)
+            if (f < nf)
+                U[di + f * FS] = v[f];
+    }
+    (void)flags;
+}
+
 }  // namespace octh

@@ -441,3 +441,44 @@ def sedov_blast(nsub: int = 8, E: int = 8, e_blast: float = 1.0, rho0: float = 1
     fields = conserved(np.full_like(r, rho0), z, z, z, p, [np.where(hot, rho0, 0.0)])
     return _tile_global(f"sedov_{N}", fields, (nsub,) * 3, E, 1.0 / N, 2, False,
                         meta=dict(e_blast=e_blast, rho0=rho0))
+
+
+def amr_box(seed: int = 1006, n_coarse: int = 4, E: int = 8, n_species: int = 5, periodic: bool = True) -> Problem:
+    """Two refinement levels in the unit box (Sec. II "Data-Structure": an
+    adaptive octree with a subgrid per leaf): n_coarse^3 level-0 subgrids of
+    E^3 cells, the central 2x2x2 of which are each replaced by 8 level-1
+    subgrids (dx halved).  The noisy gas law of the other batches is drawn
+    for every interior cell, keyed on (level, cell of the level); ghosts are
+    left to the ghost fill across levels.
+    meta: level, origin ([n, 3], in cells of each subgrid's level), n0, periodic."""
+    N0 = n_coarse * E
+    c0 = n_coarse // 2 - 1
+    subs = []
+    for sz in range(n_coarse):
+        for sy in range(n_coarse):
+            for sx in range(n_coarse):
+                if all(c0 <= v <= c0 + 1 for v in (sx, sy, sz)):
+                    continue
+                subs.append((0, sx * E, sy * E, sz * E))
+    for fz in range(4):
+        for fy in range(4):
+            for fx in range(4):
+                subs.append((1, 2 * c0 * E + fx * E, 2 * c0 * E + fy * E, 2 * c0 * E + fz * E))
+    n = len(subs)
+    nf = 6 + n_species
+    edge = np.full(n, E, np.int32)
+    off, total = layout_offsets(edge, nf)
+    U = np.zeros(total)
+    level = np.array([s[0] for s in subs], np.int32)
+    origin = np.array([s[1:] for s in subs], np.int32)
+    dx = 1.0 / (N0 * 2.0 ** level)
+    B = E + 2 * NG
+    i = np.arange(E)
+    for k, (l, ox, oy, oz) in enumerate(subs):
+        Nl = N0 << l
+        cnt = ((np.uint64(l) << np.uint64(40)) +
+               (((oz + i)[:, None, None] * Nl + (oy + i)[None, :, None]) * Nl + (ox + i)[None, None, :]).astype(np.uint64))
+        f = _noisy_gas_law(seed, cnt.reshape(-1), GAMMA, n_species).reshape(nf, E, E, E)
+        U[off[k]: off[k] + nf * B ** 3].reshape(nf, B, B, B)[:, NG:NG + E, NG:NG + E, NG:NG + E] = f
+    return Problem(f"amr_box_{N0}", edge, off, dx, level, nf, U, bc=3, nbr=None, grid=(), gamma=GAMMA,
+                   meta=dict(level=level, origin=origin, n0=N0, periodic=periodic))

@@ -1,0 +1,102 @@
+"""Ghost exchange across refinement levels on the GPU (Sec. II
+"Data-Structure": octree leaves one level coarser or finer than their
+neighbours) against the oracle: the fill bit for bit, then the RHS and one
+SSP-RK3 step on the two-level box with the fill inside the step."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_06439_gb300 import inputs
+from tests.helpers import e3s, field_errors, interior_layout
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+def _oracle_fill(p):
+    m = p.meta
+    q = p.copy()
+    oracle.amr_ghost_fill(int(p.edge[0]), q.off, q.nf, m["level"], m["origin"], m["n0"], m["periodic"], q.U)
+    return q
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_amr_fill_bitwise(periodic):
+    import torch
+    from paper_2210_06439_gb300 import binding
+    p = inputs.amr_box(periodic=periodic)
+    ref = _oracle_fill(p)
+    H = binding.Hydro.from_problem(p)
+    U = torch.from_numpy(p.U).cuda()
+    for _ in range(2):  # a second fill from filled ghosts changes nothing
+        H.fill_ghosts(U)
+        torch.cuda.synchronize()
+        assert np.array_equal(U.cpu().numpy(), ref.U)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_amr_rhs_matches_oracle(precision):
+    import torch
+    from paper_2210_06439_gb300 import binding
+    p = inputs.amr_box()
+    ref = _oracle_fill(p)
+    d_o, am_o, nb = oracle.rhs(ref.edge, ref.off, ref.dx, ref.nf, ref.U, gamma=ref.gamma)
+    assert nb == 0
+    H = binding.Hydro.from_problem(p, precision=precision)
+    U = torch.from_numpy(p.U).cuda()
+    H.fill_ghosts(U)
+    d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+    am = torch.zeros(p.n_sub, dtype=torch.float64, device="cuda")
+    H.rhs(U, d, am)
+    torch.cuda.synchronize()
+    assert H.error_flags() == 0
+    errs = field_errors(d.cpu().numpy(), d_o, p.nf, e3s(p))
+    assert np.all(errs <= TOL[precision]), errs
+    np.testing.assert_allclose(am.cpu().numpy(), am_o, rtol=1e-12 if precision == 0 else 2e-6)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_amr_rk3_step_matches_oracle(precision):
+    import torch
+    from paper_2210_06439_gb300 import binding
+    p = inputs.amr_box()
+    ref = _oracle_fill(p)
+    U0 = ref.U.copy()
+    m = p.meta
+    dts = []
+    for _ in range(2):
+        dt, fired, st = oracle.rk3_step_amr(ref.edge, ref.off, ref.dx, ref.nf, ref.U, m["level"], m["origin"],
+                                            m["n0"], m["periodic"], gamma=ref.gamma)
+        assert st == 0 and fired == 0
+        dts.append(dt)
+    H = binding.Hydro.from_problem(p, precision=precision)
+    U = torch.from_numpy(U0).cuda()
+    st = torch.cuda.Stream()
+    dg = [H.rk_step(U, stream=st) for _ in range(2)]
+    torch.cuda.synchronize()
+    assert H.error_flags() == 0
+    np.testing.assert_allclose(dg, dts, rtol=1e-12 if precision == 0 else 2e-6)
+    got = U.cpu().numpy()
+    errs = field_errors(interior_layout(got, p), interior_layout(ref.U, p), p.nf, e3s(p))
+    assert np.all(errs <= (1e-12 if precision == 0 else 1e-6)), errs
+    # ghosts left consistent with the interior by the fill inside the step
+    chk = p.copy()
+    chk.U[:] = got
+    chk = _oracle_fill(chk)
+    assert np.array_equal(chk.U, got)
+
+
+def test_set_amr_rejects_unnested_layouts():
+    from paper_2210_06439_gb300 import binding
+    p = inputs.periodic_box(nsub=2, E=8)
+    H = binding.Hydro.from_problem(p)
+    org = np.array([((s % 2) * 8, ((s // 2) % 2) * 8, (s // 4) * 8) for s in range(p.n_sub)], np.int32)
+    lev = np.zeros(p.n_sub, np.int32)
+    H.set_amr(lev, org, 16, True)  # the uniform tiling is accepted
+    with pytest.raises(binding.OctError):
+        H.set_amr(lev, org, 32, True)  # 7/8 of the root box has no subgrid
+    org2 = org.copy()
+    org2[1] = org2[0]
+    with pytest.raises(binding.OctError):
+        H.set_amr(lev, org2, 16, True)  # two subgrids on one place
