@@ -246,7 +246,7 @@ static inline int64_t fidx(int E, int f, int p, int t1, int t2)
  * Optional cell mask (NULL = all cells): only the faces of masked cells are
  * evaluated and only masked cells are written. */
 static int rhs_subgrid(const double *U, int E, double dx, const hydro_par *hp, double *dU, double *amax_out,
-                       const uint8_t *mask)
+                       const uint8_t *mask, double *faces_out)
 {
     int nf = hp->nf;
     int B = E + 2 * NG;
@@ -346,6 +346,18 @@ static int rhs_subgrid(const double *U, int E, double dx, const hydro_par *hp, d
                 }
     }
 
+    /* the face-averaged fluxes of the subgrid's own boundary faces, when
+     * asked for: face 2k (+1 for the upper side) of axis k, field f, at
+     * (t1, t2) = the two other coordinates in increasing axis order */
+    if (faces_out && !mask)
+        for (int k = 0; k < 3; k++)
+            for (int side = 0; side < 2; side++)
+                for (int f = 0; f < nf; f++)
+                    for (int t2 = 0; t2 < E; t2++)
+                        for (int t1 = 0; t1 < E; t1++)
+                            faces_out[(((int64_t)(2 * k + side) * nf + f) * E + t2) * E + t1] =
+                                Ff[k][fidx(E, f, side ? E : 0, t1, t2)];
+
     /* divergence: dU/dt = -sum_k (F_{k,+} - F_{k,-}) / dx */
     for (int f = 0; f < nf; f++)
         for (int z = 0; z < E; z++)
@@ -405,10 +417,11 @@ int oco_max_threads(void)
 }
 
 /* dU/dt for all subgrids.  amax (may be NULL) receives each subgrid's max
- * signal speed.  Returns the number of subgrids that met a non-physical
- * point state, or -1 on bad arguments. */
-int oco_rhs(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
-            double eps1, const double *U, double *dUdt, double *amax, int nthreads)
+ * signal speed; faces (may be NULL) each subgrid's boundary face fluxes,
+ * [s][6][nf][E][E] packed in subgrid order.  Returns the number of subgrids
+ * that met a non-physical point state, or -1 on bad arguments. */
+int oco_rhs_faces(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
+                  double eps1, const double *U, double *dUdt, double *amax, double *faces, int nthreads)
 {
     if (n_sub < 0 || nf < 6 || nf > 64)
         return -1;
@@ -417,18 +430,32 @@ int oco_rhs(int n_sub, const int32_t *edge, const int64_t *off, const double *dx
             return -1;
     hydro_par hp = {nf, gamma, eps1};
     int64_t *doff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_sub > 0 ? n_sub : 1));
+    int64_t *foff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_sub > 0 ? n_sub : 1));
     rhs_offsets(n_sub, edge, nf, doff);
+    int64_t o = 0;
+    for (int s = 0; s < n_sub; s++) {
+        foff[s] = o;
+        o += 6 * nf * edge[s] * edge[s];
+    }
     int nbad = 0;
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
     for (int s = 0; s < n_sub; s++) {
         double a;
-        nbad += rhs_subgrid(U + off[s], edge[s], dx[s], &hp, dUdt + doff[s], &a, NULL);
+        nbad += rhs_subgrid(U + off[s], edge[s], dx[s], &hp, dUdt + doff[s], &a, NULL,
+                            faces ? faces + foff[s] : NULL);
         if (amax)
             amax[s] = a;
     }
     free(doff);
+    free(foff);
     return nbad;
+}
+
+int oco_rhs(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
+            double eps1, const double *U, double *dUdt, double *amax, int nthreads)
+{
+    return oco_rhs_faces(n_sub, edge, off, dx, nf, gamma, eps1, U, dUdt, amax, NULL, nthreads);
 }
 
 /* dU/dt at a list of sampled cells only: samples[2*i] = subgrid index,
@@ -449,7 +476,7 @@ int oco_rhs_cells(int n_sub, const int32_t *edge, const int64_t *off, const doub
         uint8_t *mask = (uint8_t *)calloc((size_t)E * E * E, 1);
         double *dU = (double *)calloc((size_t)nf * E * E * E, sizeof(double));
         mask[ci] = 1;
-        nbad += rhs_subgrid(U + off[s], E, dx[s], &hp, dU, NULL, mask);
+        nbad += rhs_subgrid(U + off[s], E, dx[s], &hp, dU, NULL, mask, NULL);
         for (int f = 0; f < nf; f++)
             out[(int64_t)i * nf + f] = dU[(int64_t)f * E * E * E + ci];
         free(mask);
@@ -598,15 +625,10 @@ int oco_rk_combine(int stage, int n_sub, const int32_t *edge, const int64_t *off
     return 0;
 }
 
-/* One full SSP-RK3 step (reading R8) on n_sub subgrids of a common edge E.
- * dt_cap > 0 caps the CFL time step (to land on an output time).
- * bc: 0 = ghosts given (left as they are), 1/2 = ghosts refreshed from the
- * neighbour table after every stage (periodic or outflow tables are both
- * expressed by nbr).  On entry U's ghosts must be valid.  *dt_out receives
- * the dt used; *floors_out (may be NULL) the number of floor firings.
- * Returns 0, 1 if a non-physical state was met, or a negative error. */
 int oco_amr_ghost_fill(int n_sub, int E, const int64_t *off, int nf, const int32_t *lev, const int32_t *org,
                        int n0, int periodic, double *U);
+int oco_amr_reflux(int n_sub, int E, const double *dx, int nf, const int32_t *lev, const int32_t *org, int n0,
+                   int periodic, const double *faces, double *dUdt);
 
 /* amr (may be NULL): when bc == 3, the ghosts are refreshed by the ghost
  * fill across levels with amr->lev, amr->org, amr->n0, amr->periodic. */
@@ -620,6 +642,13 @@ static int rk3_step_impl(int n_sub, const int32_t *edge, const int64_t *off, con
                          const int32_t *nbr, const oco_amr *amr, double *U, int64_t total_len, double *dt_out,
                          int64_t *floors_out, int nthreads);
 
+/* One full SSP-RK3 step (reading R8) on n_sub subgrids of a common edge E.
+ * dt_cap > 0 caps the CFL time step (to land on an output time).
+ * bc: 0 = ghosts given (left as they are), 1/2 = ghosts refreshed from the
+ * neighbour table after every stage (periodic or outflow tables are both
+ * expressed by nbr).  On entry U's ghosts must be valid.  *dt_out receives
+ * the dt used; *floors_out (may be NULL) the number of floor firings.
+ * Returns 0, 1 if a non-physical state was met, or a negative error. */
 int oco_rk3_step(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
                  double eps1, double eps2, double rho_floor, double cfl, double dt_cap, int bc, const int32_t *nbr,
                  double *U, int64_t total_len, double *dt_out, int64_t *floors_out, int nthreads)
@@ -628,7 +657,9 @@ int oco_rk3_step(int n_sub, const int32_t *edge, const int64_t *off, const doubl
                          total_len, dt_out, floors_out, nthreads);
 }
 
-/* One SSP-RK3 step with the ghost fill across refinement levels (reading R14). */
+/* One SSP-RK3 step across refinement levels (readings R14, R15): after each
+ * RHS the coarse side of every coarse-fine face takes the fine fluxes, and
+ * after each stage the ghosts are refreshed by the fill across levels. */
 int oco_rk3_step_amr(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
                      double eps1, double eps2, double rho_floor, double cfl, double dt_cap, const int32_t *lev,
                      const int32_t *org, int n0, int periodic, double *U, int64_t total_len, double *dt_out,
@@ -655,14 +686,20 @@ static int rk3_step_impl(int n_sub, const int32_t *edge, const int64_t *off, con
     double *U0 = (double *)malloc(sizeof(double) * (size_t)total_len);
     double *L = (double *)malloc(sizeof(double) * (size_t)nl);
     double *amax = (double *)malloc(sizeof(double) * (size_t)n_sub);
+    double *faces = bc == 3 ? (double *)malloc(sizeof(double) * (size_t)n_sub * 6 * nf * edge[0] * edge[0]) : NULL;
     memcpy(U0, U, sizeof(double) * (size_t)total_len);
     int bad = 0;
     int64_t fired = 0;
     double dt = 0.0;
     for (int stage = 1; stage <= 3; stage++) {
-        int nb = oco_rhs(n_sub, edge, off, dx, nf, gamma, eps1, U, L, amax, nthreads);
+        int nb = oco_rhs_faces(n_sub, edge, off, dx, nf, gamma, eps1, U, L, amax, faces, nthreads);
         if (nb < 0) {
             bad = -1;
+            break;
+        }
+        if (bc == 3 &&
+            oco_amr_reflux(n_sub, edge[0], dx, nf, amr->lev, amr->org, amr->n0, amr->periodic, faces, L) != 0) {
+            bad = -2;
             break;
         }
         if (nb > 0)
@@ -687,6 +724,7 @@ static int rk3_step_impl(int n_sub, const int32_t *edge, const int64_t *off, con
     free(U0);
     free(L);
     free(amax);
+    free(faces);
     *dt_out = dt;
     if (floors_out)
         *floors_out = fired;
@@ -797,6 +835,85 @@ int oco_amr_ghost_fill(int n_sub, int E, const int64_t *off, int nf, const int32
                         }
                     }
                 }
+    }
+    return err ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Flux correction at coarse-fine faces (reading R15)                        */
+/* ------------------------------------------------------------------------ */
+
+/* With faces = the boundary face fluxes of oco_rhs_faces, replaces in dUdt
+ * the flux through every face between a cell and a finer neighbour region by
+ * the mean of the 4 fine fluxes on that face, so that what leaves the fine
+ * cells enters the coarse cell and the total is conserved.  For the coarse
+ * cell's upper face along axis k the RHS changes by (F_c - F_fine)/dx, for
+ * its lower face by (F_fine - F_c)/dx.  The fine mean adds the 4 fluxes with
+ * the first tangential index fastest, then scales by 1/4.  Cells are visited
+ * subgrid by subgrid, axis x, y, z, lower side first.  Returns 0, or -2 when
+ * a finer neighbour region does not start at a fine subgrid's face (levels
+ * overlapping). */
+int oco_amr_reflux(int n_sub, int E, const double *dx, int nf, const int32_t *lev, const int32_t *org, int n0,
+                   int periodic, const double *faces, double *dUdt)
+{
+    int64_t EE = (int64_t)E * E, E3 = EE * E;
+    int64_t fsz = 6 * (int64_t)nf * EE; /* one subgrid's face block */
+    int err = 0;
+    for (int s = 0; s < n_sub; s++) {
+        int l = lev[s];
+        int64_t nl = (int64_t)n0 << l;
+        for (int k = 0; k < 3; k++) {
+            int a1, a2;
+            transverse(k, &a1, &a2);
+            if (a1 > a2) {
+                int t = a1;
+                a1 = a2;
+                a2 = t;
+            }
+            for (int side = 0; side < 2; side++)
+                for (int t2 = 0; t2 < E; t2++)
+                    for (int t1 = 0; t1 < E; t1++) {
+                        int c[3];
+                        c[k] = side ? E - 1 : 0;
+                        c[a1] = t1;
+                        c[a2] = t2;
+                        /* the neighbour cell across the face, at this level */
+                        int64_t g[3] = {org[3 * s] + c[0], org[3 * s + 1] + c[1], org[3 * s + 2] + c[2]};
+                        g[k] += side ? 1 : -1;
+                        if (g[k] < 0 || g[k] >= nl) {
+                            if (!periodic)
+                                continue; /* root-box edge */
+                            g[k] = ((g[k] % nl) + nl) % nl;
+                        }
+                        if (find_cover(n_sub, E, lev, org, l, g) >= 0)
+                            continue;
+                        /* the finer cells on the far side of the face */
+                        int64_t fc[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
+                        if (!side)
+                            fc[k] += 1;
+                        int t = find_cover(n_sub, E, lev, org, l + 1, fc);
+                        if (t < 0)
+                            continue; /* a coarser neighbour: the fine side keeps its own flux */
+                        int64_t nk = fc[k] - org[3 * t + k];
+                        if (nk != (side ? 0 : E - 1)) {
+                            err = 1;
+                            continue;
+                        }
+                        int64_t u1 = fc[a1] - org[3 * t + a1], u2 = fc[a2] - org[3 * t + a2];
+                        const double *Ft = faces + t * fsz + (int64_t)(2 * k + (side ? 0 : 1)) * nf * EE;
+                        const double *Fs = faces + s * fsz + (int64_t)(2 * k + side) * nf * EE;
+                        int64_t ci = ((int64_t)c[2] * E + c[1]) * E + c[0];
+                        for (int f = 0; f < nf; f++) {
+                            const double *q = Ft + f * EE;
+                            double Ff = (((q[u2 * E + u1] + q[u2 * E + u1 + 1]) + q[(u2 + 1) * E + u1]) +
+                                         q[(u2 + 1) * E + u1 + 1]) *
+                                        0.25;
+                            double Fc = Fs[f * EE + (int64_t)t2 * E + t1];
+                            double *d = dUdt + (int64_t)s * nf * E3 + f * E3 + ci;
+                            *d += side ? (Fc - Ff) / dx[s] : (Ff - Fc) / dx[s];
+                        }
+                    }
+        }
     }
     return err ? -2 : 0;
 }

@@ -19,7 +19,7 @@ _OUT = os.path.join(_HERE, "_build", "liboct_oracle.so")
 __all__ = [
     "build_oracle", "lib", "ppm", "prim", "kt_point", "simpson", "rhs", "rhs_cells",
     "dt_from_amax", "ghost_fill", "floors", "rk_combine", "rk3_step", "max_threads", "amr_ghost_fill",
-    "rk3_step_amr",
+    "rk3_step_amr", "rhs_faces", "amr_reflux",
 ]
 
 _lib = None
@@ -67,6 +67,10 @@ def _declare(L):
     L.oco_max_threads.restype = _I
     L.oco_rhs.argtypes = [_I, _P, _P, _P, _I, _D, _D, _P, _P, _P, _I]
     L.oco_rhs.restype = _I
+    L.oco_rhs_faces.argtypes = [_I, _P, _P, _P, _I, _D, _D, _P, _P, _P, _P, _I]
+    L.oco_rhs_faces.restype = _I
+    L.oco_amr_reflux.argtypes = [_I, _I, _P, _I, _P, _P, _I, _I, _P, _P]
+    L.oco_amr_reflux.restype = _I
     L.oco_rhs_cells.argtypes = [_I, _P, _P, _P, _I, _D, _D, _P, _I, _P, _P, _I]
     L.oco_rhs_cells.restype = _I
     L.oco_dt_from_amax.argtypes = [_I, _P, _P, _D]
@@ -149,6 +153,36 @@ def rhs(edge, off, dx, nf, U, gamma=5.0 / 3.0, eps1=1e-3, nthreads=0):
     if nb < 0:
         raise ValueError("oracle rhs: bad arguments")
     return out, amax, nb
+
+
+def rhs_faces(edge, off, dx, nf, U, gamma=5.0 / 3.0, eps1=1e-3, nthreads=0):
+    """rhs() plus each subgrid's boundary face fluxes, [s][6][nf][E][E]
+    (face 2k + side of axis k; (t2, t1) = the other two coordinates, higher
+    axis first).  Uniform edge only."""
+    edge, off, dx, U = _i32(edge), _i64(off), _f64(dx), _f64(U)
+    n = edge.shape[0]
+    E = int(edge[0])
+    assert np.all(edge == E)
+    out = np.zeros(int(np.sum(nf * edge.astype(np.int64) ** 3)))
+    amax = np.zeros(n)
+    faces = np.zeros((n, 6, nf, E, E))
+    nb = lib().oco_rhs_faces(n, _p(edge), _p(off), _p(dx), int(nf), gamma, eps1, _p(U), _p(out), _p(amax),
+                             _p(faces), int(nthreads))
+    if nb < 0:
+        raise ValueError("oracle rhs: bad arguments")
+    return out, amax, faces, nb
+
+
+def amr_reflux(E, dx, nf, level, origin, n0, periodic, faces, dUdt):
+    """In place: the flux correction at coarse-fine faces of dUdt (packed
+    [s][f][E^3]) from the boundary face fluxes of rhs_faces."""
+    dx, lev, org = _f64(dx), _i32(level), _i32(origin).reshape(-1)
+    faces = np.ascontiguousarray(faces, np.float64)
+    assert dUdt.dtype == np.float64 and dUdt.flags.c_contiguous
+    r = lib().oco_amr_reflux(lev.shape[0], int(E), _p(dx), int(nf), _p(lev), _p(org), int(n0), int(periodic),
+                             _p(faces), _p(dUdt))
+    if r != 0:
+        raise ValueError(f"oracle amr_reflux failed ({r})")
 
 
 def rhs_cells(edge, off, dx, nf, U, samples, gamma=5.0 / 3.0, eps1=1e-3, nthreads=0):

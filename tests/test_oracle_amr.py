@@ -3,6 +3,8 @@
 level coarser or finer).  Reading: a ghost cell takes the covering cell of
 its own level, else the coarser cell that contains it (injection), else the
 mean of the 8 finer cells it contains (restriction)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -101,7 +103,6 @@ def test_uniform_state_is_steady_across_levels():
     changes no cell by more than the rounding of the restriction means and
     of the stage averages (3/4 a + 1/4 a), and the step is set by the finest
     cells (dx = 1/64)."""
-    import math
     p = inputs.amr_box(n_coarse=4, E=8)
     E, B = 8, 14
     G = p.gamma
@@ -130,3 +131,114 @@ def test_uniform_state_is_steady_across_levels():
     np.testing.assert_allclose(p.U, U0, rtol=1e-15, atol=0)
     c = math.sqrt(G * pr / rho)
     assert dt == pytest.approx(0.4 * (1.0 / 64) / (0.7 + c), rel=1e-14)
+
+
+def _volume_totals(p, d):
+    """Per field: sum over cells of dx^3 * d, and the same sum of |.|."""
+    E = int(p.edge[0])
+    dd = d.reshape(p.n_sub, p.nf, E ** 3)
+    w = (p.dx ** 3)[:, None]
+    return ([math.fsum((w * dd[:, f]).ravel()) for f in range(p.nf)],
+            [math.fsum(np.abs(w * dd[:, f]).ravel()) for f in range(p.nf)])
+
+
+def test_reflux_restores_conservation():
+    """On a periodic two-level box the volume integral of dU/dt is a sum of
+    face fluxes that cancel pairwise, except at coarse-fine faces where the
+    coarse flux differs from the fine ones.  After the flux correction every
+    field's integral vanishes to rounding; before it, it does not."""
+    p = inputs.amr_box()
+    m = p.meta
+    oracle.amr_ghost_fill(8, p.off, p.nf, m["level"], m["origin"], m["n0"], m["periodic"], p.U)
+    d, _, F, nb = oracle.rhs_faces(p.edge, p.off, p.dx, p.nf, p.U)
+    assert nb == 0
+    t, sc = _volume_totals(p, d)
+    assert all(abs(a) > 1e-6 * b for a, b in zip(t, sc))
+    oracle.amr_reflux(8, p.dx, p.nf, m["level"], m["origin"], m["n0"], m["periodic"], F, d)
+    t, sc = _volume_totals(p, d)
+    assert all(abs(a) <= 1e-14 * b for a, b in zip(t, sc)), [a / b for a, b in zip(t, sc)]
+
+
+def test_reflux_takes_the_fine_mean_at_the_coarse_face_centre():
+    """Coarse face fluxes 0, fine face fluxes a linear function of the face
+    centre (distinct dyadic coefficients per axis and field): the
+    correction of each coarse cell next to the refined block is +-F(centre of
+    its coarse face)/dx, exactly, with + for its lower face; all other cells
+    are untouched."""
+    p = inputs.amr_box(n_coarse=4, E=8)
+    E, n0 = 8, p.meta["n0"]
+    lev, org = p.meta["level"], p.meta["origin"]
+    nf = p.nf
+    axes = [(1, 2), (0, 2), (0, 1)]
+    coef = [(0.5 + f, 0.25 * (f + 1), -0.125 * (f + 2)) for f in range(nf)]
+
+    def flux(f, k, lo, hi, pn):  # tangential positions lo, hi and normal position pn, level-0 units
+        a, b, c = coef[f]
+        return a + b * lo + c * hi + 0.375 * pn + 0.0625 * k
+
+    F = np.zeros((p.n_sub, 6, nf, E, E))
+    i = np.arange(E)
+    for t in range(p.n_sub):
+        if lev[t] != 1:
+            continue
+        for k in range(3):
+            al, ah = axes[k]
+            hi, lo = np.meshgrid((org[t, ah] + i + 0.5) / 2, (org[t, al] + i + 0.5) / 2, indexing="ij")
+            for side in range(2):
+                for f in range(nf):
+                    F[t, 2 * k + side, f] = flux(f, k, lo, hi, (org[t, k] + side * E) / 2)
+    d = np.zeros(p.n_sub * nf * E ** 3)
+    oracle.amr_reflux(E, p.dx, nf, lev, org, n0, True, F, d)
+    d = d.reshape(p.n_sub, nf, E, E, E)  # [s][f][z][y][x]
+    lo_b, hi_b = (n0 // E // 2 - 1) * E, (n0 // E // 2 + 1) * E  # refined block, level-0 cells
+    want = np.zeros_like(d)
+    for s in range(p.n_sub):
+        if lev[s] != 0:
+            continue
+        for z in range(E):
+            for y in range(E):
+                for x in range(E):
+                    c = (org[s, 0] + x, org[s, 1] + y, org[s, 2] + z)
+                    for k in range(3):
+                        al, ah = axes[k]
+                        for side, step in ((0, -1), (1, 1)):
+                            if (c[k] - org[s, k]) != (E - 1 if side else 0):
+                                continue
+                            g = list(c)
+                            g[k] = (g[k] + step) % n0
+                            if not all(lo_b <= v < hi_b for v in g):
+                                continue
+                            for f in range(nf):
+                                Fc = flux(f, k, c[al] + 0.5, c[ah] + 0.5, c[k] + side)
+                                want[s, f, z, y, x] += (-Fc if side else Fc) / p.dx[s]
+    assert np.count_nonzero(want) > 0
+    np.testing.assert_array_equal(d, want)
+
+
+def test_reflux_on_one_level_changes_nothing():
+    p = inputs.periodic_box(nsub=2, E=8)
+    org = np.array([((s % 2) * 8, ((s // 2) % 2) * 8, (s // 4) * 8) for s in range(p.n_sub)], np.int32)
+    rng = np.random.default_rng(3)
+    F = rng.standard_normal((p.n_sub, 6, p.nf, 8, 8))
+    d = rng.standard_normal(p.n_sub * p.nf * 512)
+    d0 = d.copy()
+    oracle.amr_reflux(8, p.dx, p.nf, np.zeros(p.n_sub, np.int32), org, 16, True, F, d)
+    assert np.array_equal(d, d0)
+
+
+def test_amr_rk3_step_conserves():
+    """One SSP-RK3 step across levels, with the flux correction, conserves
+    mass, momentum and energy to 1e-14 on the periodic two-level box."""
+    p = inputs.amr_box()
+    m = p.meta
+    oracle.amr_ghost_fill(8, p.off, p.nf, m["level"], m["origin"], m["n0"], m["periodic"], p.U)
+    from tests.helpers import interior_layout
+    before = interior_layout(p.U, p)
+    dt, fired, st = oracle.rk3_step_amr(p.edge, p.off, p.dx, p.nf, p.U, m["level"], m["origin"], m["n0"],
+                                        m["periodic"], gamma=p.gamma)
+    assert st == 0 and fired == 0 and dt > 0
+    after = interior_layout(p.U, p)
+    t0, sc = _volume_totals(p, before)
+    t1, _ = _volume_totals(p, after)
+    for f in range(5):
+        assert abs(t1[f] - t0[f]) <= 1e-14 * sc[f], (f, (t1[f] - t0[f]) / sc[f])
