@@ -44,6 +44,10 @@ WORKLOADS = {
                         lambda inp: inp.binary_star(4)),
     "binary_star_256": ("32768 subgrids of 8^3 (256^3 outflow box), the binary-star law, 5 species",
                         lambda inp: inp.binary_star(32), lambda inp: inp.binary_star(4)),
+    "amr_box_64": ("568 subgrids of 8^3 on 2 levels: a periodic 64^3 box of level-0 subgrids whose central 16^3 "
+                   "cells are refined into 64 level-1 subgrids; ghost fill across levels and flux correction at "
+                   "coarse-fine faces; the periodic_box law, 5 species, seed 1006",
+                   lambda inp: inp.amr_box(n_coarse=8), lambda inp: inp.amr_box(n_coarse=4)),
 }
 UNIT = "cell-updates/s"
 STEP = "one step = one SSP-RK3 step (3 RHS + dt + 3 combine/floor + 3 ghost fill), FP64"
@@ -345,9 +349,16 @@ def mixed_error_table(prob, results, stream):
     import torch
     from paper_2210_06439_gb300 import binding
     ref = prob.copy()
-    if ref.bc != 0:
-        oracle.ghost_fill(int(ref.edge[0]), ref.off, ref.nf, ref.nbr, ref.U)
-    d_o, _, _ = oracle.rhs(ref.edge, ref.off, ref.dx, ref.nf, ref.U, gamma=ref.gamma)
+    if ref.bc == 3:
+        m = ref.meta
+        amr = (m["level"], m["origin"], m["n0"], m["periodic"])
+        oracle.amr_ghost_fill(int(ref.edge[0]), ref.off, ref.nf, *amr, ref.U)
+        d_o, _, F, _ = oracle.rhs_faces(ref.edge, ref.off, ref.dx, ref.nf, ref.U, gamma=ref.gamma)
+        oracle.amr_reflux(int(ref.edge[0]), ref.dx, ref.nf, *amr, F, d_o)
+    else:
+        if ref.bc != 0:
+            oracle.ghost_fill(int(ref.edge[0]), ref.off, ref.nf, ref.nbr, ref.U)
+        d_o, _, _ = oracle.rhs(ref.edge, ref.off, ref.dx, ref.nf, ref.U, gamma=ref.gamma)
     r = results[binding.OCT_MIXED]
     r["U"].copy_(r["U0"])
     r["H"].rhs(r["U"], r["dU"], stream=stream)
@@ -371,6 +382,13 @@ def _oracle_step_time(workload):
     import oracle
     from paper_2210_06439_gb300 import inputs
     p = WORKLOADS[workload][2](inputs)
+    if p.bc == 3:
+        m = p.meta
+        amr = (m["level"], m["origin"], m["n0"], m["periodic"])
+        oracle.amr_ghost_fill(int(p.edge[0]), p.off, p.nf, *amr, p.U)
+        t0 = time.perf_counter()
+        oracle.rk3_step_amr(p.edge, p.off, p.dx, p.nf, p.U, *amr, gamma=p.gamma, nthreads=0)
+        return time.perf_counter() - t0, p.n_cells, p.n_sub
     if p.bc != 0:
         oracle.ghost_fill(int(p.edge[0]), p.off, p.nf, p.nbr, p.U)
     t0 = time.perf_counter()

@@ -117,10 +117,16 @@ oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, const int64
  * level l), periodic (periodic != 0) or with outflow edges.  Each ghost cell
  * then takes: the covering cell of a subgrid at the same level (a copy); else
  * the covering cell one level coarser (prolongation by injection); else the
- * mean of the 8 cells one level finer (restriction).  No flux correction is
- * applied at coarse-fine faces.  Sets the boundary mode to OCT_BC_AMR (used
- * by oct_hydro_fill_ghosts and oct_hydro_rk_step); OCT_E_ARG when a ghost
- * cell has no source (levels not properly nested) or the arrays are invalid. */
+ * mean of the 8 cells one level finer (restriction).  In this mode the RHS
+ * (oct_hydro_rhs, oct_hydro_rhs_host and every stage of oct_hydro_rk_step)
+ * also applies the flux correction at coarse-fine faces: the coarse cell's
+ * flux through such a face is replaced by the mean of the 4 fine fluxes on
+ * it, which makes the update conservative across levels.  Sets the boundary
+ * mode to OCT_BC_AMR (used by oct_hydro_fill_ghosts and oct_hydro_rk_step);
+ * OCT_E_ARG when a ghost cell has no source (levels not properly nested),
+ * subgrids overlap, or the arrays are invalid.  Device buffers: the ghost
+ * plan (8 bytes per ghost cell) and the face fluxes of the subgrids next to
+ * a level change (48 nf E^2 bytes each), held until the layout changes. */
 oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, const int32_t *origin, int root_cells,
                              int periodic);
 

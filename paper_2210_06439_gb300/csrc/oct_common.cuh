@@ -54,6 +54,11 @@ struct RhsArgs {
     int nf;
     double gamma, eps1;
     unsigned *flags;
+    // optional boundary face fluxes (null: none): subgrid s with
+    // face_slot[s] >= 0 writes its 6 faces at faces + face_slot[s]*6*nf*E*E,
+    // [face 2k+side][f][t2][t1] with (t1, t2) its other axes in increasing order
+    double *faces;
+    const int *face_slot;
 };
 
 // ---------------------------------------------------------------------------

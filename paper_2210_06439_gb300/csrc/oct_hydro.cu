@@ -77,6 +77,11 @@ struct oct_hydro {
            *d_Lhost = nullptr;
     unsigned *d_flags = nullptr;
     int2 *d_amr_plan = nullptr;  // ghost-cell sources across levels (OCT_BC_AMR)
+    double *d_faces = nullptr;     // boundary face fluxes of the subgrids next to a level change
+    int *d_face_slot = nullptr;    // per subgrid: its slot in d_faces, or -1
+    RefluxCorr *d_corr = nullptr;  // flux corrections at coarse-fine faces, grouped by coarse cell
+    int *d_corr_first = nullptr;
+    int n_corr_cells = 0;
     std::map<const double *, GraphEntry> graphs;
 };
 
@@ -112,6 +117,11 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_Uhost);
     dfree(h->d_Lhost);
     dfree(h->d_amr_plan);
+    dfree(h->d_faces);
+    dfree(h->d_face_slot);
+    dfree(h->d_corr);
+    dfree(h->d_corr_first);
+    h->n_corr_cells = 0;
     drop_graphs(h);
 }
 
@@ -417,9 +427,91 @@ extern "C" oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, con
             plan[(size_t)s * G + q] = make_int2((int)(t | 0x80000000u), (int)local(t, cf));
         }
     }
+    // flux corrections: every face between a cell and a finer region
+    struct Pending {
+        long long cell;  // s * E^3 + interior linear index
+        int s, k, side, t, u1, u2, t1, t2;
+    };
+    std::vector<Pending> pend;
+    for (int s = 0; s < n; s++) {
+        const int l = level[s];
+        const long long nl = (long long)root_cells << l;
+        for (int k = 0; k < 3; k++) {
+            const int a1 = k == 0 ? 1 : 0, a2 = k == 2 ? 1 : 2;
+            for (int side = 0; side < 2; side++)
+                for (int t2 = 0; t2 < E; t2++)
+                    for (int t1 = 0; t1 < E; t1++) {
+                        int c[3];
+                        c[k] = side ? E - 1 : 0;
+                        c[a1] = t1;
+                        c[a2] = t2;
+                        long long g[3] = {(long long)origin[3 * s] + c[0], (long long)origin[3 * s + 1] + c[1],
+                                          (long long)origin[3 * s + 2] + c[2]};
+                        g[k] += side ? 1 : -1;
+                        if (g[k] < 0 || g[k] >= nl) {
+                            if (!periodic)
+                                continue;
+                            g[k] = ((g[k] % nl) + nl) % nl;
+                        }
+                        if (cover(l, g) >= 0)
+                            continue;
+                        long long fc[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
+                        if (!side)
+                            fc[k] += 1;
+                        const int t = cover(l + 1, fc);
+                        if (t < 0)
+                            continue;
+                        if (fc[k] - origin[3 * t + k] != (side ? 0 : E - 1))
+                            return fail(OCT_E_ARG, "subgrids %d and %d overlap across levels", s, t);
+                        pend.push_back({(long long)s * E * E * E + ((long long)c[2] * E + c[1]) * E + c[0], s, k, side,
+                                        t, (int)(fc[a1] - origin[3 * t + a1]), (int)(fc[a2] - origin[3 * t + a2]), t1,
+                                        t2});
+                    }
+        }
+    }
+    std::stable_sort(pend.begin(), pend.end(), [](const Pending &a, const Pending &b) { return a.cell < b.cell; });
+    std::vector<int> slot(n, -1);
+    int nslot = 0;
+    for (const Pending &p : pend) {
+        if (slot[p.s] < 0)
+            slot[p.s] = nslot++;
+        if (slot[p.t] < 0)
+            slot[p.t] = nslot++;
+    }
+    const long long EE = (long long)E * E, fblk = 6LL * h->nf * EE;
+    std::vector<RefluxCorr> corr;
+    std::vector<int> first;
+    for (size_t i = 0; i < pend.size(); i++) {
+        const Pending &p = pend[i];
+        if (i == 0 || p.cell != pend[i - 1].cell)
+            first.push_back((int)corr.size());
+        RefluxCorr C;
+        C.d = h->doff[p.s] + (p.cell - (long long)p.s * E * E * E);
+        C.fc = slot[p.s] * fblk + (2LL * p.k + p.side) * h->nf * EE + (long long)p.t2 * E + p.t1;
+        C.ff = slot[p.t] * fblk + (2LL * p.k + (p.side ? 0 : 1)) * h->nf * EE + (long long)p.u2 * E + p.u1;
+        C.s = p.s;
+        C.side = p.side;
+        corr.push_back(C);
+    }
+    first.push_back((int)corr.size());
     dfree(h->d_amr_plan);
+    dfree(h->d_faces);
+    dfree(h->d_face_slot);
+    dfree(h->d_corr);
+    dfree(h->d_corr_first);
+    h->n_corr_cells = 0;
     CUDA_TRY(cudaMalloc(&h->d_amr_plan, sizeof(int2) * plan.size()));
     CUDA_TRY(cudaMemcpy(h->d_amr_plan, plan.data(), sizeof(int2) * plan.size(), cudaMemcpyHostToDevice));
+    if (!corr.empty()) {
+        CUDA_TRY(cudaMalloc(&h->d_faces, sizeof(double) * nslot * fblk));
+        CUDA_TRY(cudaMalloc(&h->d_face_slot, sizeof(int) * n));
+        CUDA_TRY(cudaMalloc(&h->d_corr, sizeof(RefluxCorr) * corr.size()));
+        CUDA_TRY(cudaMalloc(&h->d_corr_first, sizeof(int) * first.size()));
+        CUDA_TRY(cudaMemcpy(h->d_face_slot, slot.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h->d_corr, corr.data(), sizeof(RefluxCorr) * corr.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h->d_corr_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
+        h->n_corr_cells = (int)first.size() - 1;
+    }
     h->bc = OCT_BC_AMR;
     drop_graphs(h);
     return OCT_OK;
@@ -503,10 +595,18 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
     A.gamma = h->gamma;
     A.eps1 = h->eps1;
     A.flags = h->d_flags;
+    const bool reflux = h->bc == OCT_BC_AMR && h->n_corr_cells > 0;
+    A.faces = reflux ? h->d_faces : nullptr;
+    A.face_slot = reflux ? h->d_face_slot : nullptr;
     const int prec = h->precision, mode = h->tile_mode;
     int grid = std::min<int>(A.n_items, h->n_sm * h->ctas_per_sm[prec][mode]);
     CUDA_TRY(rhs_launch(prec, mode, grid, st, A));
     CUDA_TRY(cudaGetLastError());
+    if (reflux) {
+        reflux_kernel<<<(h->n_corr_cells + 127) / 128, 128, 0, st>>>(dUdt, h->d_faces, h->d_corr, h->d_corr_first,
+                                                                     h->n_corr_cells, h->nf, h->edge[0], h->d_dx);
+        CUDA_TRY(cudaGetLastError());
+    }
     return OCT_OK;
 }
 
@@ -970,6 +1070,8 @@ extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_s
     A.gamma = gamma;
     A.eps1 = de_switch1;
     A.flags = flags;
+    A.faces = nullptr;
+    A.face_slot = nullptr;
     int grid = std::min(n_items, D->n_sm * D->ctas[precision]);
     CUDA_TRY(rhs_launch(precision, 0, grid, s, A));
     dt_kernel<<<1, 1024, 0, s>>>(n_items, d_items, dx, d_amax, cfl, 0.0, dt);

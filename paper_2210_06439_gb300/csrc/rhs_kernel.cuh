@@ -426,6 +426,12 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
         const double rdx = 1.0 / A.dx[s];
         const int ncin = tx * ty;
         double amax = 0.0;
+        // this subgrid's boundary face fluxes, if wanted (looked up where used:
+        // a pointer kept live across the plane loop costs registers)
+        auto face_block = [&]() -> double * {
+            const int sl = A.face_slot[s];
+            return sl >= 0 ? A.faces + (long long)sl * 6 * nf * E * E : nullptr;
+        };
 
         auto stage_plane = [&](int kz) {
             if constexpr (STAGED) {
@@ -708,6 +714,17 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                     double d = -(dxy[f * C64 + c] + dz) * rdx;
                     dUb[(long long)f * E * E * E + (long long)(kz - 1) * E * E + (long long)(y0 + j) * E + (x0 + i)] = d;
                 }
+                double *fb;
+                if (A.faces != nullptr && (kz == 1 || kz == E) && (fb = face_block()) != nullptr) {
+                    // the subgrid's -z (below plane 0) or +z (above plane E-1) face
+                    const T *zs = kz == 1 ? zm : zp;
+                    double *o = fb + (long long)(kz == 1 ? 4 : 5) * nf * E * E;
+                    for (int q = tid; q < nf * ncin; q += NTHREADS) {
+                        int f = q / ncin, c = q - f * ncin;
+                        int i = c % tx, j = c / tx;
+                        o[(long long)f * E * E + (y0 + j) * E + (x0 + i)] = Num<T>::to_d(zs[f * C64 + c]);
+                    }
+                }
             }
             __syncthreads();
             if (kz >= 1) {
@@ -724,6 +741,32 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                     double dX = Num<T>::to_d(fx[j * (tx + 1) + i + 1]) - Num<T>::to_d(fx[j * (tx + 1) + i]);
                     double dY = Num<T>::to_d(fy[(j + 1) * tx + i]) - Num<T>::to_d(fy[j * tx + i]);
                     dxy[f * C64 + c] = dX + dY;
+                }
+                double *fb;
+                if (A.faces != nullptr && (x0 == 0 || y0 == 0 || x0 + tx == E || y0 + ty == E) &&
+                    (fb = face_block()) != nullptr) {
+                    // x and y faces of plane kz on the subgrid's boundary
+                    const long long EE = (long long)E * E;
+                    if (x0 == 0 || x0 + tx == E)
+                        for (int q = tid; q < nf * ty; q += NTHREADS) {
+                            int f = q / ty, j = q - f * ty;
+                            const T *fx = faccx + f * FXS + j * (tx + 1);
+                            const long long o = f * EE + (long long)kz * E + (y0 + j);
+                            if (x0 == 0)
+                                fb[o] = Num<T>::to_d(fx[0]);
+                            if (x0 + tx == E)
+                                fb[nf * EE + o] = Num<T>::to_d(fx[tx]);
+                        }
+                    if (y0 == 0 || y0 + ty == E)
+                        for (int q = tid; q < nf * tx; q += NTHREADS) {
+                            int f = q / tx, i = q - f * tx;
+                            const T *fy = faccy + f * FYS;
+                            const long long o = f * EE + (long long)kz * E + (x0 + i);
+                            if (y0 == 0)
+                                fb[2 * nf * EE + o] = Num<T>::to_d(fy[i]);
+                            if (y0 + ty == E)
+                                fb[3 * nf * EE + o] = Num<T>::to_d(fy[ty * tx + i]);
+                        }
                 }
             }
             __syncthreads();

@@ -305,4 +305,40 @@ __global__ void amr_ghost_kernel(double *U, int E, const long long *off, int nf,
     (void)flags;
 }
 
+// One flux correction at a coarse-fine face: the coarse cell's RHS entry d
+// (field 0, in the dU/dt array) of subgrid s, its own flux on the face at fc
+// and the first of the 2x2 fine fluxes at ff (field 0, in the face array),
+// side 1 for the coarse cell's upper face.
+struct RefluxCorr {
+    long long d, fc, ff;
+    int s, side;
+};
+
+// Flux correction at coarse-fine faces: one thread per coarse cell, which
+// applies its corrections (first[i] .. first[i+1]-1, in axis order) field by
+// field: the coarse flux is replaced by the mean of the 4 fine fluxes, added
+// first-tangential-index fastest and scaled by 1/4.
+__global__ void reflux_kernel(double *dUdt, const double *faces, const RefluxCorr *corr, const int *first, int ncell,
+                              int nf, int E, const double *dx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncell)
+        return;
+    const long long EE = (long long)E * E, E3 = EE * E;
+    const int c0 = first[i], c1 = first[i + 1];
+    for (int f = 0; f < nf; f++) {
+        double *dp = dUdt + corr[c0].d + f * E3;
+        double d = *dp;
+        for (int c = c0; c < c1; c++) {
+            const RefluxCorr C = corr[c];
+            const double *q = faces + C.ff + f * EE;
+            const double Ff = (((q[0] + q[1]) + q[E]) + q[E + 1]) * 0.25;
+            const double Fc = faces[C.fc + f * EE];
+            const double h = dx[C.s];
+            d += C.side ? (Fc - Ff) / h : (Ff - Fc) / h;
+        }
+        *dp = d;
+    }
+}
+
 }  // namespace octh
