@@ -149,62 +149,80 @@ __device__ __forceinline__ float mc_slope(float a, float b)
     return same ? copysignf(r, a) : 0.f;
 }
 
-// CW84 monotonicity constraints on (um, u0, up) written with d1 = up - u0,
-// d2 = u0 - um: flat at an extremum (d1 d2 <= 0); otherwise the parabola
-// overshoots on the minus side exactly when |d2| > 2|d1| (then um = u0 - 2 d1)
-// and on the plus side when |d1| > 2|d2| (then up = u0 + 2 d2).
-__device__ __forceinline__ void cw84_limit(double u0, double &um, double &up)
+// x/2 and 2x exactly, on the exponent field of the high word while the
+// result stays a normal number; zero stays zero; otherwise by a multiply.
+__device__ __forceinline__ double half_d(double x)
 {
-    const double d1 = up - u0, d2 = u0 - um;
+    const HL X = hl(x);
+    const int e = (X.h >> 20) & 0x7FF;
+    if (e > 1 && e < 2047)
+        return from_hl(X.h - (1 << 20), X.l);
+    if (is_zero(X))
+        return x;
+    return 0.5 * x;
+}
+
+// CW84 PPM on u_{-2..2}: limited values at the cell's two ends.  The
+// parabola is carried as d1 = up - u0 and d2 = u0 - um, where up, um are the
+// interface values (u0 + u+-1)/2 - (du+-1 - du0)/6:
+//   d1 = (u1 - u0)/2 + (du0 - du1)/6,   d2 = (u0 - u-1)/2 + (du0 - du-1)/6.
+// The CW84 monotonicity constraints then act on (d1, d2): flat at an
+// extremum (d1 d2 <= 0); when |d2| > 2|d1| the parabola overshoots on the
+// minus side and d2 becomes 2 d1; when |d1| > 2|d2|, d1 becomes 2 d2.
+// Finally up = u0 + d1, um = u0 - d2.
+__device__ __forceinline__ void ppm5(double um2, double um1, double u0, double up1, double up2, double &vm,
+                                     double &vp)
+{
+    const double am2 = um1 - um2, am1 = u0 - um1, ap1 = up1 - u0, ap2 = up2 - up1;
+    const double dm = mc_slope(am2, am1);
+    const double d0 = mc_slope(am1, ap1);
+    const double dp = mc_slope(ap1, ap2);
+    const double s6 = 1.0 / 6.0;
+    double d1 = fma(d0 - dp, s6, half_d(ap1));
+    double d2 = fma(d0 - dm, s6, half_d(am1));
     const HL D1 = hl(d1), D2 = hl(d2);
     if (((D1.h ^ D2.h) < 0) || is_zero(D1) || is_zero(D2)) {
-        um = u0;
-        up = u0;
+        vm = u0;
+        vp = u0;
         return;
     }
     const int h1 = D1.h & 0x7FFFFFFF, h2 = D2.h & 0x7FFFFFFF;
     const int e1 = h1 >> 20, e2 = h2 >> 20;
-    bool A, Bp;
     if (e1 >= 1 && e1 <= 2045 && e2 >= 1 && e2 <= 2045) {
-        A = mag_lt(h1 + (1 << 20), D1.l, h2, D2.l);   // |d2| > 2|d1|
-        Bp = mag_lt(h2 + (1 << 20), D2.l, h1, D1.l);  // |d1| > 2|d2|
+        if (mag_lt(h1 + (1 << 20), D1.l, h2, D2.l))          // |d2| > 2|d1|
+            d2 = from_hl(D1.h + (1 << 20), D1.l);             // 2 d1
+        else if (mag_lt(h2 + (1 << 20), D2.l, h1, D1.l))     // |d1| > 2|d2|
+            d1 = from_hl(D2.h + (1 << 20), D2.l);             // 2 d2
     } else {
-        A = fabs(d2) > 2.0 * fabs(d1);
-        Bp = fabs(d1) > 2.0 * fabs(d2);
+        if (fabs(d2) > 2.0 * fabs(d1))
+            d2 = 2.0 * d1;
+        else if (fabs(d1) > 2.0 * fabs(d2))
+            d1 = 2.0 * d2;
     }
-    if (A)
-        um = fma(-2.0, d1, u0);
-    else if (Bp)
-        up = fma(2.0, d2, u0);
+    vp = u0 + d1;
+    vm = u0 - d2;
 }
-__device__ __forceinline__ void cw84_limit(float u0, float &um, float &up)
+
+// The FP32 form: the interface values first, then the constraints on
+// d1 = up - u0 and d2 = u0 - um formed from them.
+__device__ __forceinline__ void ppm5(float um2, float um1, float u0, float up1, float up2, float &vm, float &vp)
 {
-    float d1 = up - u0, d2 = u0 - um;
+    const float am2 = um1 - um2, am1 = u0 - um1, ap1 = up1 - u0, ap2 = up2 - up1;
+    const float dm = mc_slope(am2, am1);
+    const float d0 = mc_slope(am1, ap1);
+    const float dp = mc_slope(ap1, ap2);
+    const float s6 = 1.0f / 6.0f;
+    float up = fmaf(d0 - dp, s6, fmaf(0.5f, ap1, u0));
+    float um = fmaf(d0 - dm, -s6, fmaf(-0.5f, am1, u0));
+    const float d1 = up - u0, d2 = u0 - um;
     if (d1 * d2 <= 0.f) {
         um = u0;
         up = u0;
-        return;
-    }
-    if (fabsf(d2) > 2.f * fabsf(d1))
+    } else if (fabsf(d2) > 2.f * fabsf(d1)) {
         um = fmaf(-2.f, d1, u0);
-    else if (fabsf(d1) > 2.f * fabsf(d2))
+    } else if (fabsf(d1) > 2.f * fabsf(d2)) {
         up = fmaf(2.f, d2, u0);
-}
-
-// CW84 PPM on u_{-2..2}: limited values at the cell's two ends.  The
-// interface value (u0 + u1)/2 - (du1 - du0)/6 is formed as
-// u0 + (u1 - u0)/2 + (du0 - du1)/6.
-template <class T>
-__device__ __forceinline__ void ppm5(T um2, T um1, T u0, T up1, T up2, T &vm, T &vp)
-{
-    const T am2 = um1 - um2, am1 = u0 - um1, ap1 = up1 - u0, ap2 = up2 - up1;
-    const T dm = mc_slope(am2, am1);
-    const T d0 = mc_slope(am1, ap1);
-    const T dp = mc_slope(ap1, ap2);
-    const T s6 = T(1.0 / 6.0);
-    T up = fma(d0 - dp, s6, fma(T(0.5), ap1, u0));
-    T um = fma(d0 - dm, -s6, fma(T(-0.5), am1, u0));
-    cw84_limit(u0, um, up);
+    }
     vm = um;
     vp = up;
 }
@@ -373,7 +391,7 @@ __device__ __forceinline__ void phase_a(T *temp, const float *raw, const double 
                         u[m + 2] = Num<T>::from_d(__ldg(ub + m * st));
                 }
                 T vm, vp;
-                ppm5<T>(u[0], u[1], u[2], u[3], u[4], vm, vp);
+                ppm5(u[0], u[1], u[2], u[3], u[4], vm, vp);
                 temp[((2 * L) * nf + f) * NC + ci] = vm;
                 temp[((2 * L + 1) * nf + f) * NC + ci] = vp;
             }
@@ -625,9 +643,11 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
 #pragma unroll
                         for (int f = 0; f < MAXNF; f++)
                             acc[f] = T(0);
+                        T pacc = T(0);
                         for (int k = 0; k < G.napt; k++) {
                             const int pt = G.apt[axis][k];
-                            const T w = G.wcls[pt] == 0 ? T(16.0 / 36.0) : (G.wcls[pt] == 1 ? T(4.0 / 36.0) : T(1.0 / 36.0));
+                            // half the Simpson weight (16, 4 or 1)/36
+                            const T hw = G.wcls[pt] == 0 ? T(8.0 / 36.0) : (G.wcls[pt] == 1 ? T(2.0 / 36.0) : T(0.5 / 36.0));
                             const int ls = G.lslot[pt], rs = G.rslot[pt];
                             const T *qL, *pL_;
                             int sL;
@@ -665,21 +685,21 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                             // F_f = (F_f(L) + F_f(R))/2 - a (u_R - u_L)/2 written per side:
                             // alpha u_L + beta u_R, alpha = (v_L + a)/2, beta = (v_R - a)/2,
                             // plus the pressure terms of the normal momentum and the energy
-                            const T hw = T(0.5) * w;
                             const T al = (vkL + a) * hw;
                             const T be = (vkR - a) * hw;
 #pragma unroll
                             for (int f = 0; f < MAXNF; f++)
                                 if (f < nf)
                                     acc[f] = fma(al, qL[f * sL], fma(be, qR[f * NC], acc[f]));
-                            const T pm = (pLv + pRv) * hw;
-                            const T pe = fma(pLv, vkL, pRv * vkR) * hw;
-#pragma unroll
-                            for (int k = 0; k < 3; k++)
-                                if (k == axis)
-                                    acc[F_SX + k] += pm;
-                            acc[F_EGAS] += pe;
+                            // pressure terms: the normal momentum's once per face (below),
+                            // the energy's p v_k per point
+                            pacc = fma(pLv + pRv, hw, pacc);
+                            acc[F_EGAS] = fma(fma(pLv, vkL, pRv * vkR), hw, acc[F_EGAS]);
                         }
+#pragma unroll
+                        for (int k = 0; k < 3; k++)
+                            if (k == axis)
+                                acc[F_SX + k] += pacc;
                         T *dst = axis == 0 ? faccx : (axis == 1 ? faccy : zacc + (kz & 1) * nf * C64);
                         const int stride = axis == 2 ? C64 : (axis == 0 ? FXS : FYS);
 #pragma unroll
