@@ -255,7 +255,7 @@ def run_ours(args, rank, world):
         rhs_ms = timed(lambda: H.rhs(U, dU, stream=stream), args.steps, args.warmup)
         flags = H.error_flags()
         results[prec] = dict(step_ms=step_ms, rhs_ms=rhs_ms, flags=flags, H=H, U=U, dU=dU, U0=U0,
-                             tile_mode=H.tile_mode())
+                             launch=H.launch_info())
 
     # end to end through the host-buffer ABI call (pinned host state)
     H64 = results[binding.OCT_FP64]["H"]
@@ -329,7 +329,8 @@ def run_ours(args, rank, world):
         "gpu_launches": launches_per_step(prob) * K,
         "clocks": clocks,
         "error_flags": {"fp64": s64["flags"], "mixed": smx["flags"]},
-        "tile_mode": {"fp64": s64["tile_mode"], "mixed": smx["tile_mode"]},
+        "launch": {k: {"tile_mode": r["launch"][0], "ctas_per_sm": r["launch"][1], "work_items": r["launch"][2]}
+                   for k, r in (("fp64", s64), ("mixed", smx))},
     }
     if mixed_err is not None:
         out["mixed"]["max_rel_err_per_field_vs_oracle"] = mixed_err

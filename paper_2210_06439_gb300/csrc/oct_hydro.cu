@@ -67,7 +67,8 @@ struct oct_hydro {
     std::vector<long long> cell_begin;  // packed interior-cell offset of each subgrid
     long long state_len = 0, rhs_len = 0;
     int tile_mode = 0;       // 0: 8x8 tiles (6x6 for edge 12); 1: 8x4 tiles (6x4 for edge 12)
-    int ctas_per_sm[2][2] = {{0, 0}, {0, 0}};  // [precision][tile mode]
+    int ctas_per_sm[2][2] = {{0, 0}, {0, 0}};  // [precision][tile mode]: the occupancy limit
+    int cta_use[2][2] = {{0, 0}, {0, 0}};      // resident CTAs per SM of the persistent grid (0: the limit)
     // device memory
     int *d_edge = nullptr, *d_nbr = nullptr, *d_item_begin = nullptr;
     long long *d_off = nullptr, *d_doff = nullptr, *d_cell_begin = nullptr;
@@ -599,7 +600,8 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
     A.faces = reflux ? h->d_faces : nullptr;
     A.face_slot = reflux ? h->d_face_slot : nullptr;
     const int prec = h->precision, mode = h->tile_mode;
-    int grid = std::min<int>(A.n_items, h->n_sm * h->ctas_per_sm[prec][mode]);
+    const int per_sm = h->cta_use[prec][mode] > 0 ? h->cta_use[prec][mode] : h->ctas_per_sm[prec][mode];
+    int grid = std::min<int>(A.n_items, h->n_sm * per_sm);
     CUDA_TRY(rhs_launch(prec, mode, grid, st, A));
     CUDA_TRY(cudaGetLastError());
     if (reflux) {
@@ -838,33 +840,42 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
+    // candidates: tile shape (threads per subgrid) x resident CTAs per SM of
+    // the persistent grid; each timed on 2 launches after one untimed
     float best = 1e30f;
-    int best_mode = h->tile_mode;
+    const int prec = h->precision;
+    int best_mode = h->tile_mode, best_use = h->cta_use[prec][h->tile_mode];
     for (int mode = 0; mode < 2; mode++) {
         h->tile_mode = mode;
         build_items(h);
         if ((st = upload_items(h)) != OCT_OK)
             return st;
-        float tot = 0.0f;
-        for (int rep = 0; rep < 4; rep++) {
-            CUDA_TRY(cudaEventRecord(e0, s));
-            if ((st = launch_rhs(h, U_sample, h->d_L, s)) != OCT_OK)
-                return st;
-            CUDA_TRY(cudaEventRecord(e1, s));
-            CUDA_TRY(cudaEventSynchronize(e1));
-            float ms;
-            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0)
-                tot += ms;
+        for (int use = 1; use <= h->ctas_per_sm[prec][mode]; use++) {
+            h->cta_use[prec][mode] = use;
+            float tot = 0.0f;
+            for (int rep = 0; rep < 3; rep++) {
+                CUDA_TRY(cudaEventRecord(e0, s));
+                if ((st = launch_rhs(h, U_sample, h->d_L, s)) != OCT_OK)
+                    return st;
+                CUDA_TRY(cudaEventRecord(e1, s));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float ms;
+                CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0)
+                    tot += ms;
+            }
+            if (tot < best) {
+                best = tot;
+                best_mode = mode;
+                best_use = use;
+            }
         }
-        if (tot < best) {
-            best = tot;
-            best_mode = mode;
-        }
+        h->cta_use[prec][mode] = 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->tile_mode = best_mode;
+    h->cta_use[prec][best_mode] = best_use;
     build_items(h);
     drop_graphs(h);
     return upload_items(h);
@@ -877,8 +888,10 @@ extern "C" oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *
         return st;
     if (tile_mode)
         *tile_mode = h->tile_mode;
-    if (ctas_per_sm)
-        *ctas_per_sm = h->ctas_per_sm[h->precision][h->tile_mode];
+    if (ctas_per_sm) {
+        const int use = h->cta_use[h->precision][h->tile_mode];
+        *ctas_per_sm = use > 0 ? use : h->ctas_per_sm[h->precision][h->tile_mode];
+    }
     if (n_items)
         *n_items = (int)h->items.size();
     return OCT_OK;

@@ -180,3 +180,31 @@ def test_nonphysical_input_sets_flag_without_trap():
     torch.cuda.synchronize()
     assert H.error_flags() & 1
     assert H.error_flags() == 0  # read-and-clear
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rk3_step_with_floor_firings_matches_oracle(precision):
+    """The last species slightly below zero (-1e-9 rho) in the lower-x half
+    of the periodic box: the floors (rho_i >= 0 after every stage) fire on
+    both sides, the GPU raises the floor flag and no other, and the stepped
+    state matches the oracle's."""
+    torch = _torch()
+    p = inputs.periodic_box(nsub=2)
+    for s in range(p.n_sub):
+        if s % 2 == 0:  # subgrids with x origin 0
+            blk = p.block(s)
+            blk[10] = -1e-9 * blk[0]
+    ref = oracle_filled(p)
+    U0 = ref.U.copy()
+    dt_o, fired, st = oracle.rk3_step(ref.edge, ref.off, ref.dx, ref.nf, ref.U, bc=1, nbr=ref.nbr)
+    assert st == 0 and fired > 0
+    H = _hydro(p, precision)
+    U = torch.from_numpy(U0).cuda()
+    dt_g = H.rk_step(U)
+    flags = H.error_flags()
+    assert flags & 2 and not flags & 1
+    assert dt_g == pytest.approx(dt_o, rel=1e-12 if precision == 0 else MIXED_SPEED_RTOL)
+    got = U.cpu().numpy()
+    errs = field_errors(interior_layout(got, p), interior_layout(ref.U, p), p.nf, e3s(p))
+    assert np.all(errs <= (1e-12 if precision == 0 else 1e-6)), errs
+    assert np.all(interior_layout(got, p).reshape(p.n_sub, p.nf, -1)[:, 6:] >= 0.0)
