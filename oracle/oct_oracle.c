@@ -42,8 +42,14 @@
  *       interior cell (zero-gradient outflow);
  *   R14 ghost fill across refinement levels: the same-level cell if one
  *       covers the ghost, else the covering coarser cell (injection), else
- *       the mean of the 8 finer cells (restriction); no flux correction at
- *       coarse-fine faces.
+ *       the mean of the 8 finer cells (restriction);
+ *   R15 flux correction at coarse-fine faces: the coarse flux through such
+ *       a face is replaced by the mean of the 4 fine fluxes on it;
+ *   R16 (optional, recon = 1) primitive reconstruction: PPM acts on
+ *       w = (rho, v, p, tau, X_i = rho_i / rho) of every cell, and each point
+ *       is turned back into conserved fields (s = rho v,
+ *       E = p / (gamma - 1) + rho |v|^2 / 2, rho_i = rho X_i) with its v, p
+ *       taken as reconstructed; the cell's p uses the dual-energy switch.
  *
  * Field order: rho, s_x, s_y, s_z, E_gas, tau, rho_1 .. rho_ns.
  * State layout: one ghosted block per subgrid, structure of arrays
@@ -153,13 +159,11 @@ static double phys_flux(int k, int f, const double *q, const double *v, double p
 
 /* Kurganov-Tadmor central flux at one quadrature point (reading R5):
  * F = (F_k(qL) + F_k(qR))/2 - a (qR - qL)/2 with the local speed
- * a = max(|v_k,L| + c_L, |v_k,R| + c_R).  Writes F[0..nf-1] and *a_out. */
-int oco_kt_point(int k, int nf, const double *qL, const double *qR, double gamma, double eps1,
-                 double *F, double *a_out)
+ * a = max(|v_k,L| + c_L, |v_k,R| + c_R), from both sides' conserved fields
+ * q and primitives v, p, c.  Writes F[0..nf-1]; returns a. */
+static double kt_flux(int k, int nf, const double *qL, const double *vL, double pL, double cL, const double *qR,
+                      const double *vR, double pR, double cR, double *F)
 {
-    double vL[3], vR[3], pL, pR, cL, cR;
-    int bad = oco_prim(qL, gamma, eps1, vL, &pL, &cL);
-    bad |= oco_prim(qR, gamma, eps1, vR, &pR, &cR);
     double aL = fabs(vL[k]) + cL;
     double aR = fabs(vR[k]) + cR;
     double a = fmax(aL, aR);
@@ -168,8 +172,61 @@ int oco_kt_point(int k, int nf, const double *qL, const double *qR, double gamma
         double FR = phys_flux(k, f, qR, vR, pR);
         F[f] = 0.5 * (FL + FR) - 0.5 * a * (qR[f] - qL[f]);
     }
-    *a_out = a;
+    return a;
+}
+
+/* The same from the conserved fields alone (primitives by oco_prim).
+ * Writes F[0..nf-1] and *a_out. */
+int oco_kt_point(int k, int nf, const double *qL, const double *qR, double gamma, double eps1,
+                 double *F, double *a_out)
+{
+    double vL[3], vR[3], pL, pR, cL, cR;
+    int bad = oco_prim(qL, gamma, eps1, vL, &pL, &cL);
+    bad |= oco_prim(qR, gamma, eps1, vR, &pR, &cR);
+    *a_out = kt_flux(k, nf, qL, vL, pL, cL, qR, vR, pR, cR, F);
     return bad;
+}
+
+/* Reading R16, cell side: the variables reconstructed in primitive mode,
+ * w = (rho, v_x, v_y, v_z, p, tau, X_1 .. X_ns) with X_i = rho_i / rho, from
+ * a cell's conserved fields q (p by oco_prim, with the dual-energy switch).
+ * Returns 1 for a non-physical cell. */
+static int cell_prim(const double *q, int nf, double gamma, double eps1, double *w)
+{
+    double v[3], p, c;
+    int bad = oco_prim(q, gamma, eps1, v, &p, &c);
+    w[F_RHO] = q[F_RHO];
+    w[F_SX] = v[0];
+    w[F_SY] = v[1];
+    w[F_SZ] = v[2];
+    w[F_EGAS] = p;
+    w[F_TAU] = q[F_TAU];
+    for (int f = F_SPC; f < nf; f++)
+        w[f] = q[f] / q[F_RHO];
+    return bad;
+}
+
+/* Reading R16, point side: conserved fields q and primitives v, p, c of a
+ * point from its reconstructed w.  Returns 1 for a non-physical point
+ * (rho <= 0 or a non-finite sound speed). */
+static int point_from_prim(const double *w, int nf, double gamma, double *q, double *v, double *p_out, double *c_out)
+{
+    double rho = w[F_RHO], p = w[F_EGAS];
+    v[0] = w[F_SX];
+    v[1] = w[F_SY];
+    v[2] = w[F_SZ];
+    q[F_RHO] = rho;
+    q[F_SX] = rho * v[0];
+    q[F_SY] = rho * v[1];
+    q[F_SZ] = rho * v[2];
+    q[F_EGAS] = p / (gamma - 1.0) + 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    q[F_TAU] = w[F_TAU];
+    for (int f = F_SPC; f < nf; f++)
+        q[f] = rho * w[f];
+    double c = sqrt(gamma * p / rho);
+    *p_out = p;
+    *c_out = c;
+    return (!(rho > 0.0) || !isfinite(c)) ? 1 : 0;
 }
 
 /* Tensor Simpson (closed Newton-Cotes, degree 2) over the 3x3 face points
@@ -216,6 +273,7 @@ static double point_value(const double *Uf, int B, int x, int y, int z, const in
 typedef struct {
     int nf;
     double gamma, eps1;
+    int recon; /* 0: conserved fields (R1), 1: primitive variables (R16) */
 } hydro_par;
 
 /* Transverse axes of face normal k, in increasing order. */
@@ -284,6 +342,27 @@ static int rhs_subgrid(const double *U, int E, double dx, const hydro_par *hp, d
                 }
             }
 
+    /* primitive mode (R16): the reconstructed variables w of every cell of
+     * the ghosted block, and which cells are not physical */
+    const double *R = U;
+    double *Wb = NULL;
+    uint8_t *badc = NULL;
+    int bad = 0;
+    if (hp->recon) {
+        int64_t B3 = (int64_t)B * B * B;
+        Wb = (double *)malloc(sizeof(double) * (size_t)(nf * B3));
+        badc = (uint8_t *)calloc((size_t)B3, 1);
+        double q[64], w[64];
+        for (int64_t c = 0; c < B3; c++) {
+            for (int f = 0; f < nf; f++)
+                q[f] = U[f * fs + c];
+            badc[c] = (uint8_t)cell_prim(q, nf, hp->gamma, hp->eps1, w);
+            for (int f = 0; f < nf; f++)
+                Wb[f * fs + c] = w[f];
+        }
+        R = Wb;
+    }
+
     /* step 1, reconstruct: point value of every field at x + d/2 for all 26
      * directions d of every needed cell */
     for (int z = -1; z <= E; z++)
@@ -300,14 +379,16 @@ static int rhs_subgrid(const double *U, int E, double dx, const hydro_par *hp, d
                                 continue;
                             for (int f = 0; f < nf; f++)
                                 Q[(ci * 27 + dir_index(d)) * nf + f] =
-                                    point_value(U + f * fs, B, x + NG, y + NG, z + NG, d);
+                                    point_value(R + f * fs, B, x + NG, y + NG, z + NG, d);
+                            if (badc)
+                                for (int m = -2; m <= 2; m++)
+                                    bad |= badc[cidx(B, x + NG + m * ddx, y + NG + m * dy, z + NG + m * dz)];
                         }
             }
 
     /* step 2, flux: KT at the 9 quadrature points of each needed face, then
      * the Simpson face average */
     double amax = 0.0;
-    int bad = 0;
     double Fq[9][64];
     for (int k = 0; k < 3; k++) {
         int a1, a2;
@@ -334,7 +415,14 @@ static int rhs_subgrid(const double *U, int E, double dx, const hydro_par *hp, d
                         const double *qL = Q + (iL * 27 + dir_index(dL)) * nf;
                         const double *qR = Q + (iR * 27 + dir_index(dR)) * nf;
                         double a;
-                        bad |= oco_kt_point(k, nf, qL, qR, hp->gamma, hp->eps1, Fq[q], &a);
+                        if (hp->recon) {
+                            double uL[64], uR[64], vL[3], vR[3], pL, pR, cL, cR;
+                            bad |= point_from_prim(qL, nf, hp->gamma, uL, vL, &pL, &cL);
+                            bad |= point_from_prim(qR, nf, hp->gamma, uR, vR, &pR, &cR);
+                            a = kt_flux(k, nf, uL, vL, pL, cL, uR, vR, pR, cR, Fq[q]);
+                        } else {
+                            bad |= oco_kt_point(k, nf, qL, qR, hp->gamma, hp->eps1, Fq[q], &a);
+                        }
                         amax = fmax(amax, a);
                     }
                     for (int f = 0; f < nf; f++) {
@@ -377,6 +465,8 @@ static int rhs_subgrid(const double *U, int E, double dx, const hydro_par *hp, d
     }
     free(needc);
     free(Q);
+    free(Wb);
+    free(badc);
     if (amax_out)
         *amax_out = amax;
     return bad;
@@ -420,15 +510,15 @@ int oco_max_threads(void)
  * signal speed; faces (may be NULL) each subgrid's boundary face fluxes,
  * [s][6][nf][E][E] packed in subgrid order.  Returns the number of subgrids
  * that met a non-physical point state, or -1 on bad arguments. */
-int oco_rhs_faces(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
-                  double eps1, const double *U, double *dUdt, double *amax, double *faces, int nthreads)
+static int rhs_all(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
+                   double eps1, int recon, const double *U, double *dUdt, double *amax, double *faces, int nthreads)
 {
     if (n_sub < 0 || nf < 6 || nf > 64)
         return -1;
     for (int s = 0; s < n_sub; s++)
         if (!valid_edge(edge[s]))
             return -1;
-    hydro_par hp = {nf, gamma, eps1};
+    hydro_par hp = {nf, gamma, eps1, recon};
     int64_t *doff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_sub > 0 ? n_sub : 1));
     int64_t *foff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_sub > 0 ? n_sub : 1));
     rhs_offsets(n_sub, edge, nf, doff);
@@ -452,10 +542,24 @@ int oco_rhs_faces(int n_sub, const int32_t *edge, const int64_t *off, const doub
     return nbad;
 }
 
+int oco_rhs_faces(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
+                  double eps1, const double *U, double *dUdt, double *amax, double *faces, int nthreads)
+{
+    return rhs_all(n_sub, edge, off, dx, nf, gamma, eps1, 0, U, dUdt, amax, faces, nthreads);
+}
+
+/* dU/dt with the reconstructed variables chosen by recon (0: conserved
+ * fields, reading R1; 1: primitive variables, reading R16). */
+int oco_rhs_recon(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
+                  double eps1, int recon, const double *U, double *dUdt, double *amax, int nthreads)
+{
+    return rhs_all(n_sub, edge, off, dx, nf, gamma, eps1, recon, U, dUdt, amax, NULL, nthreads);
+}
+
 int oco_rhs(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
             double eps1, const double *U, double *dUdt, double *amax, int nthreads)
 {
-    return oco_rhs_faces(n_sub, edge, off, dx, nf, gamma, eps1, U, dUdt, amax, NULL, nthreads);
+    return rhs_all(n_sub, edge, off, dx, nf, gamma, eps1, 0, U, dUdt, amax, NULL, nthreads);
 }
 
 /* dU/dt at a list of sampled cells only: samples[2*i] = subgrid index,
@@ -466,7 +570,7 @@ int oco_rhs_cells(int n_sub, const int32_t *edge, const int64_t *off, const doub
 {
     if (nf < 6 || nf > 64)
         return -1;
-    hydro_par hp = {nf, gamma, eps1};
+    hydro_par hp = {nf, gamma, eps1, 0};
     int nbad = 0;
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
@@ -639,8 +743,8 @@ typedef struct {
 
 static int rk3_step_impl(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
                          double eps1, double eps2, double rho_floor, double cfl, double dt_cap, int bc,
-                         const int32_t *nbr, const oco_amr *amr, double *U, int64_t total_len, double *dt_out,
-                         int64_t *floors_out, int nthreads);
+                         const int32_t *nbr, const oco_amr *amr, int recon, double *U, int64_t total_len,
+                         double *dt_out, int64_t *floors_out, int nthreads);
 
 /* One full SSP-RK3 step (reading R8) on n_sub subgrids of a common edge E.
  * dt_cap > 0 caps the CFL time step (to land on an output time).
@@ -653,8 +757,19 @@ int oco_rk3_step(int n_sub, const int32_t *edge, const int64_t *off, const doubl
                  double eps1, double eps2, double rho_floor, double cfl, double dt_cap, int bc, const int32_t *nbr,
                  double *U, int64_t total_len, double *dt_out, int64_t *floors_out, int nthreads)
 {
-    return rk3_step_impl(n_sub, edge, off, dx, nf, gamma, eps1, eps2, rho_floor, cfl, dt_cap, bc, nbr, NULL, U,
+    return rk3_step_impl(n_sub, edge, off, dx, nf, gamma, eps1, eps2, rho_floor, cfl, dt_cap, bc, nbr, NULL, 0, U,
                          total_len, dt_out, floors_out, nthreads);
+}
+
+/* oco_rk3_step with the reconstructed variables chosen by recon (0:
+ * conserved fields, reading R1; 1: primitive variables, reading R16). */
+int oco_rk3_step_recon(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
+                       double eps1, double eps2, double rho_floor, double cfl, double dt_cap, int bc,
+                       const int32_t *nbr, int recon, double *U, int64_t total_len, double *dt_out,
+                       int64_t *floors_out, int nthreads)
+{
+    return rk3_step_impl(n_sub, edge, off, dx, nf, gamma, eps1, eps2, rho_floor, cfl, dt_cap, bc, nbr, NULL, recon,
+                         U, total_len, dt_out, floors_out, nthreads);
 }
 
 /* One SSP-RK3 step across refinement levels (readings R14, R15): after each
@@ -666,14 +781,14 @@ int oco_rk3_step_amr(int n_sub, const int32_t *edge, const int64_t *off, const d
                      int64_t *floors_out, int nthreads)
 {
     oco_amr a = {lev, org, n0, periodic};
-    return rk3_step_impl(n_sub, edge, off, dx, nf, gamma, eps1, eps2, rho_floor, cfl, dt_cap, 3, NULL, &a, U,
+    return rk3_step_impl(n_sub, edge, off, dx, nf, gamma, eps1, eps2, rho_floor, cfl, dt_cap, 3, NULL, &a, 0, U,
                          total_len, dt_out, floors_out, nthreads);
 }
 
 static int rk3_step_impl(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
                          double eps1, double eps2, double rho_floor, double cfl, double dt_cap, int bc,
-                         const int32_t *nbr, const oco_amr *amr, double *U, int64_t total_len, double *dt_out,
-                         int64_t *floors_out, int nthreads)
+                         const int32_t *nbr, const oco_amr *amr, int recon, double *U, int64_t total_len,
+                         double *dt_out, int64_t *floors_out, int nthreads)
 {
     if (n_sub <= 0)
         return -1;
@@ -692,7 +807,7 @@ static int rk3_step_impl(int n_sub, const int32_t *edge, const int64_t *off, con
     int64_t fired = 0;
     double dt = 0.0;
     for (int stage = 1; stage <= 3; stage++) {
-        int nb = oco_rhs_faces(n_sub, edge, off, dx, nf, gamma, eps1, U, L, amax, faces, nthreads);
+        int nb = rhs_all(n_sub, edge, off, dx, nf, gamma, eps1, recon, U, L, amax, faces, nthreads);
         if (nb < 0) {
             bad = -1;
             break;

@@ -67,6 +67,10 @@ def _declare(L):
     L.oco_max_threads.restype = _I
     L.oco_rhs.argtypes = [_I, _P, _P, _P, _I, _D, _D, _P, _P, _P, _I]
     L.oco_rhs.restype = _I
+    L.oco_rhs_recon.argtypes = [_I, _P, _P, _P, _I, _D, _D, _I, _P, _P, _P, _I]
+    L.oco_rhs_recon.restype = _I
+    L.oco_rk3_step_recon.argtypes = [_I, _P, _P, _P, _I, _D, _D, _D, _D, _D, _D, _I, _P, _I, _P, _I64, _P, _P, _I]
+    L.oco_rk3_step_recon.restype = _I
     L.oco_rhs_faces.argtypes = [_I, _P, _P, _P, _I, _D, _D, _P, _P, _P, _P, _I]
     L.oco_rhs_faces.restype = _I
     L.oco_amr_reflux.argtypes = [_I, _I, _P, _I, _P, _P, _I, _I, _P, _P]
@@ -142,14 +146,15 @@ def simpson(Fq):
     return float(lib().oco_simpson(_p(f)))
 
 
-def rhs(edge, off, dx, nf, U, gamma=5.0 / 3.0, eps1=1e-3, nthreads=0):
-    """dU/dt of all subgrids; returns (dUdt packed [s][f][E^3], amax[s], n_bad)."""
+def rhs(edge, off, dx, nf, U, gamma=5.0 / 3.0, eps1=1e-3, nthreads=0, recon=0):
+    """dU/dt of all subgrids; returns (dUdt packed [s][f][E^3], amax[s], n_bad).
+    recon: 0 reconstructs the conserved fields, 1 the primitive variables."""
     edge, off, dx, U = _i32(edge), _i64(off), _f64(dx), _f64(U)
     n = edge.shape[0]
     out = np.zeros(int(np.sum(nf * edge.astype(np.int64) ** 3)))
     amax = np.zeros(n)
-    nb = lib().oco_rhs(n, _p(edge), _p(off), _p(dx), int(nf), gamma, eps1, _p(U), _p(out), _p(amax),
-                       int(nthreads))
+    nb = lib().oco_rhs_recon(n, _p(edge), _p(off), _p(dx), int(nf), gamma, eps1, int(recon), _p(U), _p(out),
+                             _p(amax), int(nthreads))
     if nb < 0:
         raise ValueError("oracle rhs: bad arguments")
     return out, amax, nb
@@ -227,8 +232,9 @@ def rk_combine(stage, edge, off, nf, dt, U0, L, U):
 
 
 def rk3_step(edge, off, dx, nf, U, bc, nbr=None, gamma=5.0 / 3.0, eps1=1e-3, eps2=0.1,
-             rho_floor=1e-12, cfl=0.4, dt_cap=0.0, nthreads=0):
-    """One SSP-RK3 step in place; returns (dt, floor firings, status)."""
+             rho_floor=1e-12, cfl=0.4, dt_cap=0.0, nthreads=0, recon=0):
+    """One SSP-RK3 step in place; returns (dt, floor firings, status).
+    recon: 0 reconstructs the conserved fields, 1 the primitive variables."""
     edge, off, dx = _i32(edge), _i64(off), _f64(dx)
     assert U.dtype == np.float64 and U.flags.c_contiguous
     n = edge.shape[0]
@@ -236,8 +242,9 @@ def rk3_step(edge, off, dx, nf, U, bc, nbr=None, gamma=5.0 / 3.0, eps1=1e-3, eps
         nbr = np.full(26 * n, -1, np.int32)
     nbr = _i32(nbr)
     dt, fired = np.zeros(1), np.zeros(1, np.int64)
-    st = lib().oco_rk3_step(n, _p(edge), _p(off), _p(dx), int(nf), gamma, eps1, eps2, rho_floor, cfl,
-                            float(dt_cap), int(bc), _p(nbr), _p(U), U.size, _p(dt), _p(fired), int(nthreads))
+    st = lib().oco_rk3_step_recon(n, _p(edge), _p(off), _p(dx), int(nf), gamma, eps1, eps2, rho_floor, cfl,
+                                  float(dt_cap), int(bc), _p(nbr), int(recon), _p(U), U.size, _p(dt), _p(fired),
+                                  int(nthreads))
     return float(dt[0]), int(fired[0]), int(st)
 
 
