@@ -208,7 +208,7 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
 
     def make(precision):
-        H = binding.Hydro.from_problem(prob, precision=precision)
+        H = binding.Hydro.from_problem(prob, precision=precision, recon=args.recon)
         U = torch.from_numpy(prob.U).cuda()
         with torch.cuda.stream(stream):
             H.fill_ghosts(U, stream=stream)
@@ -305,7 +305,8 @@ def run_ours(args, rank, world):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded generators of paper_2210_06439_gb300.inputs)",
-        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; {STEP}", "subgrids": prob.n_sub,
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; {STEP}"
+                               + ("; primitive reconstruction" if args.recon else ""), "subgrids": prob.n_sub,
                    "edges": sorted(set(int(e) for e in prob.edge)), "ghost": 3, "n_species": prob.n_species,
                    "interior_cells": n_cells, "parallelism": f"replicas x{world}",
                    "l2": "flushed (256 MiB write) before each timed step"},
@@ -326,7 +327,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": world * n_cells / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes + 8,
                 "how": "oct_hydro_rk_steps_host on pinned host state: H2D copy, RK3 step, D2H copy, per step"},
-        "gpu_launches": launches_per_step(prob) * K,
+        "gpu_launches": launches_per_step(prob, args.recon) * K,
         "clocks": clocks,
         "error_flags": {"fp64": s64["flags"], "mixed": smx["flags"]},
         "launch": {k: {"tile_mode": r["launch"][0], "ctas_per_sm": r["launch"][1], "work_items": r["launch"][2]}
@@ -379,11 +380,12 @@ def mixed_error_table(prob, results, stream):
     return out
 
 
-def launches_per_step(prob):
+def launches_per_step(prob, recon=0):
     """Kernels of one graph-replayed RK3 step: 3 RHS, the dt reduction, 3
-    combines, 3 ghost fills unless ghosts are given, and 3 flux corrections
-    when the batch spans refinement levels."""
-    return 3 + 1 + 3 + (3 if prob.bc != 0 else 0) + (3 if prob.bc == 3 else 0)
+    combines, 3 ghost fills unless ghosts are given, 3 flux corrections when
+    the batch spans refinement levels, and 3 primitive-variable passes with
+    primitive reconstruction."""
+    return 3 + 1 + 3 + (3 if prob.bc != 0 else 0) + (3 if prob.bc == 3 else 0) + (3 if recon else 0)
 
 
 def _oracle_step_time(workload):
@@ -447,6 +449,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="periodic_box_64", choices=sorted(WORKLOADS))
+    ap.add_argument("--recon", type=int, default=0, choices=(0, 1),
+                    help="reconstructed variables: 0 the conserved fields (the method's default), 1 primitive")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

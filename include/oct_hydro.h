@@ -78,6 +78,7 @@ typedef enum {
 typedef enum { OCT_FP64 = 0, OCT_MIXED = 1 } oct_precision;
 
 typedef enum { OCT_BC_GIVEN = 0, OCT_BC_PERIODIC = 1, OCT_BC_OUTFLOW = 2, OCT_BC_AMR = 3 } oct_bc;
+typedef enum { OCT_RECON_CONSERVED = 0, OCT_RECON_PRIMITIVE = 1 } oct_recon;
 
 /* Device error flags (oct_hydro_get_error_flags). */
 #define OCT_FLAG_NONPHYS 0x1u /* rho <= 0 or non-finite value at a point   */
@@ -129,6 +130,19 @@ oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, const int64
  * a level change (48 nf E^2 bytes each), held until the layout changes. */
 oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, const int32_t *origin, int root_cells,
                              int periodic);
+
+/* Which variables PPM reconstructs (Sec. II "Solvers": the reconstruct
+ * kernel yields point values of the evolved variables at 26 points per cell;
+ * which variables it interpolates is not stated).  OCT_RECON_CONSERVED (the default): the conserved fields
+ * themselves.  OCT_RECON_PRIMITIVE: w = (rho, v, p, tau, X_i = rho_i / rho)
+ * of every cell (p from the dual-energy switch), each point turned back into
+ * conserved fields (s = rho v, E = p / (gamma - 1) + rho |v|^2 / 2,
+ * rho_i = rho X_i) with its reconstructed v and p used in the flux; this
+ * costs one extra pass over the state per RHS and a device buffer of
+ * oct_hydro_state_len doubles (allocated here or with the layout).
+ * OCT_E_ARG for another value.  Both precisions support both choices; the
+ * allocation-free entry point reconstructs the conserved fields only. */
+oct_status oct_hydro_set_reconstruction(oct_hydro_t h, int variables);
 
 /* Numerical parameters: precision (oct_precision: FP64 everywhere, or
  * reconstruction/flux arithmetic in FP32 with FP64 divergence, update,

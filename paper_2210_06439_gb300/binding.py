@@ -17,6 +17,7 @@ from . import build as _build
 OCT_OK, OCT_E_ARG, OCT_E_CUDA, OCT_E_NONPHYS, OCT_E_TIMEOUT, OCT_E_NOMEM, OCT_E_STATE = 0, -1, -2, -3, -4, -5, -6
 OCT_FP64, OCT_MIXED = 0, 1
 OCT_BC_GIVEN, OCT_BC_PERIODIC, OCT_BC_OUTFLOW, OCT_BC_AMR = 0, 1, 2, 3
+OCT_RECON_CONSERVED, OCT_RECON_PRIMITIVE = 0, 1
 OCT_FLAG_NONPHYS, OCT_FLAG_FLOOR = 0x1, 0x2
 
 _P = ctypes.c_void_p
@@ -29,6 +30,7 @@ SIGNATURES = {
     "oct_hydro_create": (_I, [_I, _I, _I, _I, _D, ctypes.POINTER(_P)]),
     "oct_hydro_set_layout": (_I, [_P, _P, _P, _P, _P, _P, _I]),
     "oct_hydro_set_amr": (_I, [_P, _P, _P, _I, _I]),
+    "oct_hydro_set_reconstruction": (_I, [_P, _I]),
     "oct_hydro_set_params": (_I, [_P, _I, _D, _D, _D, _D]),
     "oct_hydro_set_dt_cap": (_I, [_P, _D]),
     "oct_hydro_state_len": (_I64, [_P]),
@@ -119,7 +121,8 @@ class Hydro:
         self.n_subgrids = int(n_subgrids)
 
     @classmethod
-    def from_problem(cls, prob, precision=OCT_FP64, cfl=0.4, rho_floor=1e-12, eps1=1e-3, eps2=0.1):
+    def from_problem(cls, prob, precision=OCT_FP64, cfl=0.4, rho_floor=1e-12, eps1=1e-3, eps2=0.1,
+                     recon=OCT_RECON_CONSERVED):
         """Handle for an ``inputs.Problem`` (layout copied from it)."""
         edges = np.ascontiguousarray(prob.edge, np.int32)
         uniform = bool(np.all(edges == edges[0]))
@@ -129,6 +132,8 @@ class Hydro:
             m = prob.meta
             self.set_amr(m["level"], m["origin"], m["n0"], m["periodic"])
         self.set_params(precision, cfl, rho_floor, eps1, eps2)
+        if recon != OCT_RECON_CONSERVED:
+            self.set_reconstruction(recon)
         return self
 
     def close(self):
@@ -156,6 +161,9 @@ class Hydro:
         self._amr = [np.ascontiguousarray(level, np.int32), np.ascontiguousarray(origin, np.int32).reshape(-1)]
         check(self.L.oct_hydro_set_amr(self.h, self._amr[0].ctypes.data, self._amr[1].ctypes.data, int(root_cells),
                                        int(bool(periodic))))
+
+    def set_reconstruction(self, variables):
+        check(self.L.oct_hydro_set_reconstruction(self.h, int(variables)))
 
     def set_params(self, precision=OCT_FP64, cfl=0.4, rho_floor=1e-12, eps1=1e-3, eps2=0.1):
         check(self.L.oct_hydro_set_params(self.h, int(precision), float(cfl), float(rho_floor), float(eps1),

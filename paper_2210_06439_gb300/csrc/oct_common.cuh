@@ -53,6 +53,7 @@ struct RhsArgs {
     int n_items;
     int nf;
     double gamma, eps1;
+    double inv_gm1;                // 1 / (gamma - 1)
     unsigned *flags;
     // optional boundary face fluxes (null: none): subgrid s with
     // face_slot[s] >= 0 writes its 6 faces at faces + face_slot[s]*6*nf*E*E,

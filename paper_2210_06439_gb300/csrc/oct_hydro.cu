@@ -67,8 +67,11 @@ struct oct_hydro {
     std::vector<long long> cell_begin;  // packed interior-cell offset of each subgrid
     long long state_len = 0, rhs_len = 0;
     int tile_mode = 0;       // 0: 8x8 tiles (6x6 for edge 12); 1: 8x4 tiles (6x4 for edge 12)
-    int ctas_per_sm[2][2] = {{0, 0}, {0, 0}};  // [precision][tile mode]: the occupancy limit
-    int cta_use[2][2] = {{0, 0}, {0, 0}};      // resident CTAs per SM of the persistent grid (0: the limit)
+    // [form][tile mode], form = precision + 2 * recon
+    int ctas_per_sm[4][2] = {};  // the occupancy limit
+    int cta_use[4][2] = {};      // resident CTAs per SM of the persistent grid (0: the limit)
+    int recon = OCT_RECON_CONSERVED;
+    double *d_Wprim = nullptr;   // primitive variables of the state (primitive reconstruction)
     // device memory
     int *d_edge = nullptr, *d_nbr = nullptr, *d_item_begin = nullptr;
     long long *d_off = nullptr, *d_doff = nullptr, *d_cell_begin = nullptr;
@@ -122,23 +125,26 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_face_slot);
     dfree(h->d_corr);
     dfree(h->d_corr_first);
+    dfree(h->d_Wprim);
     h->n_corr_cells = 0;
     drop_graphs(h);
 }
 
 static oct_status set_kernel_attrs(oct_hydro *h)
 {
-    for (int prec = 0; prec < 2; prec++)
+    for (int form = 0; form < 4; form++)
         for (int mode = 0; mode < 2; mode++) {
             int nb = 0;
-            CUDA_TRY(rhs_prepare(prec, mode, h->nf, &nb));
+            CUDA_TRY(rhs_prepare(form, mode, h->nf, &nb));
             if (nb < 1)
                 return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM (%zu bytes shared memory)",
-                            rhs_smem_bytes(h->nf, prec, mode));
-            h->ctas_per_sm[prec][mode] = nb;
+                            rhs_smem_bytes(h->nf, form, mode));
+            h->ctas_per_sm[form][mode] = nb;
         }
     return OCT_OK;
 }
+
+static int form_of(const oct_hydro *h) { return h->precision + 2 * h->recon; }
 
 static void build_items(oct_hydro *h)
 {
@@ -330,7 +336,22 @@ extern "C" oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, 
     oct_status st = upload_items(h);
     if (st != OCT_OK)
         return st;
+    if (h->recon == OCT_RECON_PRIMITIVE)
+        CUDA_TRY(cudaMalloc(&h->d_Wprim, sizeof(double) * h->state_len));
     h->layout_ok = true;
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_set_reconstruction(oct_hydro_t h, int variables)
+{
+    if (!h)
+        return fail(OCT_E_ARG, "handle is NULL");
+    if (variables != OCT_RECON_CONSERVED && variables != OCT_RECON_PRIMITIVE)
+        return fail(OCT_E_ARG, "variables must be OCT_RECON_CONSERVED or OCT_RECON_PRIMITIVE (got %d)", variables);
+    if (variables == OCT_RECON_PRIMITIVE && h->layout_ok && !h->d_Wprim)
+        CUDA_TRY(cudaMalloc(&h->d_Wprim, sizeof(double) * h->state_len));
+    h->recon = variables;
+    drop_graphs(h);
     return OCT_OK;
 }
 
@@ -595,14 +616,23 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
     A.nf = h->nf;
     A.gamma = h->gamma;
     A.eps1 = h->eps1;
+    A.inv_gm1 = 1.0 / (h->gamma - 1.0);
     A.flags = h->d_flags;
+    if (h->recon == OCT_RECON_PRIMITIVE) {
+        if (!h->d_Wprim)
+            return fail(OCT_E_STATE, "no buffer for the primitive variables");
+        prim_cells_kernel<<<h->n_sub, 256, 0, st>>>(U, h->d_Wprim, h->d_edge, h->d_off, h->nf, h->gamma, h->eps1,
+                                                    h->d_flags);
+        CUDA_TRY(cudaGetLastError());
+        A.U = h->d_Wprim;
+    }
     const bool reflux = h->bc == OCT_BC_AMR && h->n_corr_cells > 0;
     A.faces = reflux ? h->d_faces : nullptr;
     A.face_slot = reflux ? h->d_face_slot : nullptr;
-    const int prec = h->precision, mode = h->tile_mode;
-    const int per_sm = h->cta_use[prec][mode] > 0 ? h->cta_use[prec][mode] : h->ctas_per_sm[prec][mode];
+    const int form = form_of(h), mode = h->tile_mode;
+    const int per_sm = h->cta_use[form][mode] > 0 ? h->cta_use[form][mode] : h->ctas_per_sm[form][mode];
     int grid = std::min<int>(A.n_items, h->n_sm * per_sm);
-    CUDA_TRY(rhs_launch(prec, mode, grid, st, A));
+    CUDA_TRY(rhs_launch(form, mode, grid, st, A));
     CUDA_TRY(cudaGetLastError());
     if (reflux) {
         reflux_kernel<<<(h->n_corr_cells + 127) / 128, 128, 0, st>>>(dUdt, h->d_faces, h->d_corr, h->d_corr_first,
@@ -843,7 +873,7 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
     // candidates: tile shape (threads per subgrid) x resident CTAs per SM of
     // the persistent grid; each timed on 2 launches after one untimed
     float best = 1e30f;
-    const int prec = h->precision;
+    const int prec = form_of(h);
     int best_mode = h->tile_mode, best_use = h->cta_use[prec][h->tile_mode];
     for (int mode = 0; mode < 2; mode++) {
         h->tile_mode = mode;
@@ -889,8 +919,8 @@ extern "C" oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *
     if (tile_mode)
         *tile_mode = h->tile_mode;
     if (ctas_per_sm) {
-        const int use = h->cta_use[h->precision][h->tile_mode];
-        *ctas_per_sm = use > 0 ? use : h->ctas_per_sm[h->precision][h->tile_mode];
+        const int use = h->cta_use[form_of(h)][h->tile_mode];
+        *ctas_per_sm = use > 0 ? use : h->ctas_per_sm[form_of(h)][h->tile_mode];
     }
     if (n_items)
         *n_items = (int)h->items.size();
@@ -1083,6 +1113,7 @@ extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_s
     A.gamma = gamma;
     A.eps1 = de_switch1;
     A.flags = flags;
+    A.inv_gm1 = 1.0 / (gamma - 1.0);
     A.faces = nullptr;
     A.face_slot = nullptr;
     int grid = std::min(n_items, D->n_sm * D->ctas[precision]);

@@ -278,6 +278,24 @@ __device__ __forceinline__ void prim_point(const float *q, float gamma, float gm
     bad |= !(rho > 0.f) || !(c == c);
 }
 
+// Primitive reconstruction (the optional variable choice): the point holds
+// w = (rho, v, p, tau, X_i); its sound speed c = sqrt(gamma p / rho) and
+// whether it is physical (rho > 0, c finite).
+__device__ __forceinline__ double sound_from_w(double rho, double p, double gamma, bool &bad)
+{
+    const double c2 = gamma * p * rcp_nr(rho);
+    const int ch = __double2hiint(c2), rh = __double2hiint(rho);
+    bad |= !(rh > 0 && rh < 0x7FF00000) || !(ch >= 0 && ch < 0x7FF00000);
+    return (ch > 0 && ch < 0x7FF00000) ? sqrt_nr(c2) : (is_zero(hl(c2)) ? 0.0 : sqrt(c2));
+}
+__device__ __forceinline__ float sound_from_w(float rho, float p, float gamma, bool &bad)
+{
+    const float c2 = gamma * p * __fdividef(1.f, rho);
+    const float c = c2 > 0.f ? c2 * rsqrtf(c2) : sqrtf(c2);
+    bad |= !(rho > 0.f) || !(c == c);
+    return c;
+}
+
 // Shared-memory plan of one CTA (dynamic shared memory) for a tile capacity
 // of txm x tym cells and nf fields.
 struct SmemPlan {
@@ -399,7 +417,11 @@ __device__ __forceinline__ void phase_a(T *temp, const float *raw, const double 
     }
 }
 
-template <class T, bool STAGED, int TXM, int TYM, int MINB>
+// PRIM: the state array holds the primitive variables w of every cell
+// (rho, v, p, tau, X_i) and PPM reconstructs them; each point is turned back
+// into conserved fields (s = rho v, E = p/(gamma-1) + rho |v|^2/2,
+// rho_i = rho X_i) with its reconstructed v and p kept for the flux.
+template <class T, bool STAGED, int TXM, int TYM, int MINB, bool PRIM>
 __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -431,6 +453,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
     const T gm1 = Num<T>::from_d(A.gamma - 1.0);
     const T ggm1 = Num<T>::from_d(A.gamma * (A.gamma - 1.0));
     const T eps1 = Num<T>::from_d(A.eps1);
+    const T inv_gm1 = Num<T>::from_d(A.inv_gm1);
     constexpr int RWX = TXM + 2 * NG, RWY = TYM + 2 * NG;  // staged plane shape
     bool bad = false;
 
@@ -597,12 +620,29 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                                 e = ly > 0 ? 0 : 1;
                         }
                         const int slot = 2 * l + e;
-                        T qh[6];
-#pragma unroll
-                        for (int f = 0; f < 6; f++)
-                            qh[f] = temp[(slot * nf + f) * NC + ci];
                         T v[3], p, cs;
-                        prim_point(qh, gamma, gm1, ggm1, eps1, v, p, cs, bad);
+                        if constexpr (PRIM) {
+                            // w -> conserved fields in place, v and p as reconstructed
+                            T *q = temp + slot * nf * NC + ci;
+                            const T rho = q[0];
+                            v[0] = q[NC];
+                            v[1] = q[2 * NC];
+                            v[2] = q[3 * NC];
+                            p = q[4 * NC];
+                            cs = sound_from_w(rho, p, gamma, bad);
+                            q[NC] = rho * v[0];
+                            q[2 * NC] = rho * v[1];
+                            q[3 * NC] = rho * v[2];
+                            q[4 * NC] = fma(T(0.5) * rho, fma(v[2], v[2], fma(v[1], v[1], v[0] * v[0])), p * inv_gm1);
+                            for (int f = F_SPC; f < nf; f++)
+                                q[f * NC] = rho * q[f * NC];
+                        } else {
+                            T qh[6];
+#pragma unroll
+                            for (int f = 0; f < 6; f++)
+                                qh[f] = temp[(slot * nf + f) * NC + ci];
+                            prim_point(qh, gamma, gm1, ggm1, eps1, v, p, cs, bad);
+                        }
                         T *o = pr + slot * 5 * NC + ci;
                         o[0] = v[0];
                         o[NC] = v[1];
@@ -666,6 +706,14 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                                 const T *pR_ = pr + rs * 5 * NC + cr;
                                 vkL = pL_[axis * sL], pLv = pL_[3 * sL], cL = pL_[4 * sL];
                                 vkR = pR_[axis * NC], pRv = pR_[3 * NC], cR = pR_[4 * NC];
+                            } else if constexpr (PRIM) {
+                                // w on both sides: v and p as reconstructed
+                                vkL = qL[(1 + axis) * sL];
+                                pLv = qL[4 * sL];
+                                cL = sound_from_w(qL[0], pLv, gamma, bad);
+                                vkR = qR[(1 + axis) * NC];
+                                pRv = qR[4 * NC];
+                                cR = sound_from_w(qR[0], pRv, gamma, bad);
                             } else {
                                 // primitives of both sides on the spot (cheap in FP32)
                                 T qh[6], v[3];
@@ -687,10 +735,33 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                             // plus the pressure terms of the normal momentum and the energy
                             const T al = (vkL + a) * hw;
                             const T be = (vkR - a) * hw;
+                            if constexpr (PRIM && !SHARED_PRIMS) {
+                                // conserved fields of both sides from w, field by field
+                                const T rL = qL[0], rR = qR[0];
+                                const T vxL = qL[sL], vyL = qL[2 * sL], vzL = qL[3 * sL];
+                                const T vxR = qR[NC], vyR = qR[2 * NC], vzR = qR[3 * NC];
 #pragma unroll
-                            for (int f = 0; f < MAXNF; f++)
-                                if (f < nf)
-                                    acc[f] = fma(al, qL[f * sL], fma(be, qR[f * NC], acc[f]));
+                                for (int f = 0; f < MAXNF; f++)
+                                    if (f < nf) {
+                                        T uL, uR;
+                                        if (f == F_RHO) {
+                                            uL = rL, uR = rR;
+                                        } else if (f == F_EGAS) {
+                                            uL = fma(T(0.5) * rL, fma(vzL, vzL, fma(vyL, vyL, vxL * vxL)), pLv * inv_gm1);
+                                            uR = fma(T(0.5) * rR, fma(vzR, vzR, fma(vyR, vyR, vxR * vxR)), pRv * inv_gm1);
+                                        } else if (f == F_TAU) {
+                                            uL = qL[f * sL], uR = qR[f * NC];
+                                        } else {  // momenta and species: rho times v or X
+                                            uL = rL * qL[f * sL], uR = rR * qR[f * NC];
+                                        }
+                                        acc[f] = fma(al, uL, fma(be, uR, acc[f]));
+                                    }
+                            } else {
+#pragma unroll
+                                for (int f = 0; f < MAXNF; f++)
+                                    if (f < nf)
+                                        acc[f] = fma(al, qL[f * sL], fma(be, qR[f * NC], acc[f]));
+                            }
                             // pressure terms: the normal momentum's once per face (below),
                             // the energy's p v_k per point
                             pacc = fma(pLv + pRv, hw, pacc);

@@ -1,6 +1,7 @@
 // rhs_launch.h -- host launchers of the RHS kernel instances.  Each instance
-// (FP64 or mixed, tile capacity 8x8 or 8x4) is compiled in a translation unit
-// of its own (rhs_<form>_<capacity>.cu) so the four build in parallel.
+// (FP64 or mixed, tile capacity 8x8 or 8x4, conserved or primitive
+// reconstruction) is compiled in a translation unit of its own
+// (rhs_<form>_<capacity>[_prim].cu) so the eight build in parallel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -8,11 +9,12 @@
 
 namespace octh {
 
-// precision: 0 FP64, 1 mixed; mode: 0 tile capacity 8x8 (one CTA per SM),
-// 1 capacity 8x4 (two CTAs per SM for FP64, three for the mixed form).
-size_t rhs_smem_bytes(int nf, int precision, int mode);
+// form: precision (0 FP64, 1 mixed) + 2 for primitive reconstruction; mode:
+// 0 tile capacity 8x8 (one CTA per SM), 1 capacity 8x4 (two CTAs per SM for
+// FP64, three for the mixed form).
+size_t rhs_smem_bytes(int nf, int form, int mode);
 bool build_group_tables(GroupTab *groups);
-cudaError_t rhs_prepare(int precision, int mode, int nf, int *ctas_per_sm);
-cudaError_t rhs_launch(int precision, int mode, int grid, cudaStream_t stream, const RhsArgs &args);
+cudaError_t rhs_prepare(int form, int mode, int nf, int *ctas_per_sm);
+cudaError_t rhs_launch(int form, int mode, int grid, cudaStream_t stream, const RhsArgs &args);
 
 }  // namespace octh

@@ -341,4 +341,43 @@ __global__ void reflux_kernel(double *dUdt, const double *faces, const RefluxCor
     }
 }
 
+// Primitive variables for reconstruction, one ghosted block per CTA:
+// w = (rho, v, p, tau, X_i = rho_i / rho) of every cell, ghosts included,
+// in the layout of the state.  p comes from the dual-energy switch: the
+// kinetic remainder e = E - |s|^2 / (2 rho), or tau^gamma when e < eps1 E.
+// A cell with rho not positive and finite, or p negative or not finite,
+// raises the non-physical flag (bit 0).
+__global__ void prim_cells_kernel(const double *U, double *W, const int *edge, const long long *off, int nf,
+                                  double gamma, double eps1, unsigned *flags)
+{
+    const int s = blockIdx.x;
+    const int B = edge[s] + 2 * NG;
+    const long long FS = (long long)B * B * B;
+    const double *u = U + off[s];
+    double *w = W + off[s];
+    bool bad = false;
+    for (long long c = threadIdx.x; c < FS; c += blockDim.x) {
+        const double rho = u[c], sx = u[FS + c], sy = u[2 * FS + c], sz = u[3 * FS + c];
+        const double E = u[4 * FS + c], tau = u[5 * FS + c];
+        const double ir = rcp_nr(rho);
+        const double vx = sx * ir, vy = sy * ir, vz = sz * ir;
+        double ei = fma(-0.5, fma(sz, vz, fma(sy, vy, sx * vx)), E);
+        if (ei < eps1 * E)
+            ei = pow(tau, gamma);
+        const double p = (gamma - 1.0) * ei;
+        w[c] = rho;
+        w[FS + c] = vx;
+        w[2 * FS + c] = vy;
+        w[3 * FS + c] = vz;
+        w[4 * FS + c] = p;
+        w[5 * FS + c] = tau;
+        for (int f = F_SPC; f < nf; f++)
+            w[f * FS + c] = u[f * FS + c] * ir;
+        const int rh = __double2hiint(rho), ph = __double2hiint(p);
+        bad |= !(rh > 0 && rh < 0x7FF00000) || !(ph >= 0 && ph < 0x7FF00000);
+    }
+    if (bad)
+        atomicOr(flags, 1u);  // non-physical state
+}
+
 }  // namespace octh
