@@ -548,6 +548,14 @@ int oco_rhs_faces(int n_sub, const int32_t *edge, const int64_t *off, const doub
     return rhs_all(n_sub, edge, off, dx, nf, gamma, eps1, 0, U, dUdt, amax, faces, nthreads);
 }
 
+/* oco_rhs_faces with the reconstructed variables chosen by recon. */
+int oco_rhs_faces_recon(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
+                        double eps1, int recon, const double *U, double *dUdt, double *amax, double *faces,
+                        int nthreads)
+{
+    return rhs_all(n_sub, edge, off, dx, nf, gamma, eps1, recon, U, dUdt, amax, faces, nthreads);
+}
+
 /* dU/dt with the reconstructed variables chosen by recon (0: conserved
  * fields, reading R1; 1: primitive variables, reading R16). */
 int oco_rhs_recon(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,

@@ -73,6 +73,8 @@ def _declare(L):
     L.oco_rk3_step_recon.restype = _I
     L.oco_rhs_faces.argtypes = [_I, _P, _P, _P, _I, _D, _D, _P, _P, _P, _P, _I]
     L.oco_rhs_faces.restype = _I
+    L.oco_rhs_faces_recon.argtypes = [_I, _P, _P, _P, _I, _D, _D, _I, _P, _P, _P, _P, _I]
+    L.oco_rhs_faces_recon.restype = _I
     L.oco_amr_reflux.argtypes = [_I, _I, _P, _I, _P, _P, _I, _I, _P, _P]
     L.oco_amr_reflux.restype = _I
     L.oco_rhs_cells.argtypes = [_I, _P, _P, _P, _I, _D, _D, _P, _I, _P, _P, _I]
@@ -160,7 +162,7 @@ def rhs(edge, off, dx, nf, U, gamma=5.0 / 3.0, eps1=1e-3, nthreads=0, recon=0):
     return out, amax, nb
 
 
-def rhs_faces(edge, off, dx, nf, U, gamma=5.0 / 3.0, eps1=1e-3, nthreads=0):
+def rhs_faces(edge, off, dx, nf, U, gamma=5.0 / 3.0, eps1=1e-3, nthreads=0, recon=0):
     """rhs() plus each subgrid's boundary face fluxes, [s][6][nf][E][E]
     (face 2k + side of axis k; (t2, t1) = the other two coordinates, higher
     axis first).  Uniform edge only."""
@@ -171,8 +173,8 @@ def rhs_faces(edge, off, dx, nf, U, gamma=5.0 / 3.0, eps1=1e-3, nthreads=0):
     out = np.zeros(int(np.sum(nf * edge.astype(np.int64) ** 3)))
     amax = np.zeros(n)
     faces = np.zeros((n, 6, nf, E, E))
-    nb = lib().oco_rhs_faces(n, _p(edge), _p(off), _p(dx), int(nf), gamma, eps1, _p(U), _p(out), _p(amax),
-                             _p(faces), int(nthreads))
+    nb = lib().oco_rhs_faces_recon(n, _p(edge), _p(off), _p(dx), int(nf), gamma, eps1, int(recon), _p(U),
+                                   _p(out), _p(amax), _p(faces), int(nthreads))
     if nb < 0:
         raise ValueError("oracle rhs: bad arguments")
     return out, amax, faces, nb

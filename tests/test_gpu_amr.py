@@ -130,3 +130,41 @@ def test_set_amr_rejects_unnested_layouts():
     org2[1] = org2[0]
     with pytest.raises(binding.OctError):
         H.set_amr(lev, org2, 16, True)  # two subgrids on one place
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_amr_rhs_primitive_reconstruction(precision):
+    """The two variable choices compose with the levels: primitive
+    reconstruction on the two-level box, flux correction included."""
+    import torch
+    from paper_2210_06439_gb300 import binding
+    p = inputs.amr_box()
+    ref = _oracle_fill(p)
+    m = p.meta
+    d_o, am_o, F, nb = oracle.rhs_faces(ref.edge, ref.off, ref.dx, ref.nf, ref.U, gamma=ref.gamma, recon=1)
+    assert nb == 0
+    oracle.amr_reflux(8, ref.dx, ref.nf, m["level"], m["origin"], m["n0"], m["periodic"], F, d_o)
+    H = binding.Hydro.from_problem(p, precision=precision, recon=binding.OCT_RECON_PRIMITIVE)
+    U = torch.from_numpy(p.U).cuda()
+    H.fill_ghosts(U)
+    d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+    am = torch.zeros(p.n_sub, dtype=torch.float64, device="cuda")
+    H.rhs(U, d, am)
+    torch.cuda.synchronize()
+    assert H.error_flags() == 0
+    errs = field_errors(d.cpu().numpy(), d_o, p.nf, e3s(p))
+    assert np.all(errs <= TOL[precision]), errs
+    np.testing.assert_allclose(am.cpu().numpy(), am_o, rtol=1e-12 if precision == 0 else MIXED_SPEED_RTOL)
+
+
+@pytest.mark.parametrize("E", [12, 16])
+def test_amr_fill_bitwise_larger_edges(E):
+    import torch
+    from paper_2210_06439_gb300 import binding
+    p = inputs.amr_box(n_coarse=4, E=E, n_species=1)
+    ref = _oracle_fill(p)
+    H = binding.Hydro.from_problem(p)
+    U = torch.from_numpy(p.U).cuda()
+    H.fill_ghosts(U)
+    torch.cuda.synchronize()
+    assert np.array_equal(U.cpu().numpy(), ref.U)
