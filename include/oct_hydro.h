@@ -10,7 +10,8 @@
  * takes three hydro iterations (Sec. V-B).  The paper gives no equations; the
  * readings used here are:
  *   - the conserved fields (rho, s_x, s_y, s_z, E_gas, tau, rho_1..rho_ns)
- *     are reconstructed;
+ *     are reconstructed (primitive variables on request, see
+ *     oct_hydro_set_reconstruction);
  *   - PPM: Colella-Woodward 1984 interface values with monotonised-central
  *     slopes and the CW84 monotonicity constraints;
  *   - the 26 points are the 6 face centres, 12 edge midpoints and 8 corners of
@@ -133,8 +134,8 @@ oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, const int32_t 
 
 /* Which variables PPM reconstructs (Sec. II "Solvers": the reconstruct
  * kernel yields point values of the evolved variables at 26 points per cell;
- * which variables it interpolates is not stated).  OCT_RECON_CONSERVED (the default): the conserved fields
- * themselves.  OCT_RECON_PRIMITIVE: w = (rho, v, p, tau, X_i = rho_i / rho)
+ * which variables it interpolates is not stated).  OCT_RECON_CONSERVED (the
+ * default): the conserved fields themselves.  OCT_RECON_PRIMITIVE: w = (rho, v, p, tau, X_i = rho_i / rho)
  * of every cell (p from the dual-energy switch), each point turned back into
  * conserved fields (s = rho v, E = p / (gamma - 1) + rho |v|^2 / 2,
  * rho_i = rho X_i) with its reconstructed v and p used in the flux; this
@@ -164,6 +165,7 @@ int64_t oct_hydro_rhs_len(oct_hydro_t h);
  * plus the finite-volume divergence): reads U (ghosts used as they are),
  * writes dUdt = -sum_k (F_k,+ - F_k,-)/dx for every interior cell and, when
  * amax is not NULL, each subgrid's max signal speed (n_subgrids doubles).
+ * After oct_hydro_set_amr the coarse-fine flux correction is part of it.
  * U and dUdt must not overlap. */
 oct_status oct_hydro_rhs(oct_hydro_t h, const double *U, double *dUdt, double *amax, void *cuda_stream);
 
@@ -180,7 +182,8 @@ oct_status oct_hydro_fill_ghosts(oct_hydro_t h, double *U, void *cuda_stream);
 /* One SSP-RK3 time step in place (three hydro iterations per time step,
  * Sec. V-B): dt from U's signal speeds, three RHS evaluations, combines,
  * floors and dual-energy re-synchronisation, and a ghost fill after each
- * stage (unless OCT_BC_GIVEN).  On entry U's ghosts must be valid.  The
+ * stage (unless OCT_BC_GIVEN; across levels, with the flux correction in
+ * each RHS, after oct_hydro_set_amr).  On entry U's ghosts must be valid.  The
  * sequence is replayed from a CUDA graph captured on first use for this U.
  * When dt_used_host_out is not NULL the stream is synchronised and the dt
  * used is written there. */
@@ -195,8 +198,10 @@ oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int n_steps, d
                                    void *cuda_stream);
 oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_host, void *cuda_stream);
 
-/* Times the candidate launch shapes (tile shape, CTAs per SM) of the RHS
- * kernel on U_sample and keeps the fastest for this layout and precision. */
+/* Times the candidate launch shapes of the RHS kernel on U_sample -- tile
+ * capacity (8x8 or 8x4 cells per work item) x resident CTAs per SM (1 up to
+ * the occupancy limit) -- and keeps the fastest for this layout, precision
+ * and reconstruction choice.  Drops captured graphs. */
 oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, void *cuda_stream);
 
 /* Allocation-free RHS + CFL dt (the paper has no counterpart: this is a

@@ -1,9 +1,10 @@
 """Runs the RHS kernel a few times on one workload, for profiling under ncu.
 
-  python -m paper_2210_06439_gb300.profile_rhs --precision 0 --nsub 8 --reps 3 [--autotune]
+  python -m paper_2210_06439_gb300.profile_rhs --precision 0 --nsub 8 --reps 3 [--autotune] [--recon 1]
 
-precision 0 = FP64, 1 = mixed; the workload is the periodic box of nsub^3
-subgrids of 8^3 cells with 5 species (ghosts filled on the device)."""
+precision 0 = FP64, 1 = mixed; recon 0 = conserved-field reconstruction,
+1 = primitive; the workload is the periodic box of nsub^3 subgrids of 8^3
+cells with 5 species (ghosts filled on the device)."""
 import argparse
 
 import torch
@@ -17,10 +18,11 @@ def main():
     ap.add_argument("--nsub", type=int, default=8)
     ap.add_argument("--edge", type=int, default=8)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--autotune", action="store_true", help="run the autotuner first (8 trial launches)")
+    ap.add_argument("--autotune", action="store_true", help="run the autotuner first (trial launches)")
+    ap.add_argument("--recon", type=int, default=0, choices=(0, 1))
     a = ap.parse_args()
     p = inputs.periodic_box(nsub=a.nsub, E=a.edge)
-    H = binding.Hydro.from_problem(p, precision=a.precision)
+    H = binding.Hydro.from_problem(p, precision=a.precision, recon=a.recon)
     U = torch.from_numpy(p.U).cuda()
     H.fill_ghosts(U)
     if a.autotune:
