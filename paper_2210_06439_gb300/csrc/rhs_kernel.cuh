@@ -142,11 +142,11 @@ __device__ __forceinline__ double mc_slope(double a, double b)
 }
 __device__ __forceinline__ float mc_slope(float a, float b)
 {
-    float s = a + b;
-    float m = fminf(fabsf(a), fabsf(b));
-    float r = fminf(0.5f * fabsf(s), 2.0f * m);
-    bool same = (a > 0.f && b > 0.f) || (a < 0.f && b < 0.f);
-    return same ? copysignf(r, a) : 0.f;
+    // same strict sign <=> a b > 0 (a product below the FP32 range counts as
+    // a sign change: such differences are far below the form's resolution)
+    const float s = a + b;
+    const float r = fminf(0.5f * fabsf(s), 2.0f * fminf(fabsf(a), fabsf(b)));
+    return a * b > 0.f ? copysignf(r, s) : 0.f;
 }
 
 // x/2 and 2x exactly, on the exponent field of the high word while the
@@ -212,19 +212,16 @@ __device__ __forceinline__ void ppm5(float um2, float um1, float u0, float up1, 
     const float d0 = mc_slope(am1, ap1);
     const float dp = mc_slope(ap1, ap2);
     const float s6 = 1.0f / 6.0f;
-    float up = fmaf(d0 - dp, s6, fmaf(0.5f, ap1, u0));
-    float um = fmaf(d0 - dm, -s6, fmaf(-0.5f, am1, u0));
+    const float up = fmaf(d0 - dp, s6, fmaf(0.5f, ap1, u0));
+    const float um = fmaf(d0 - dm, -s6, fmaf(-0.5f, am1, u0));
     const float d1 = up - u0, d2 = u0 - um;
-    if (d1 * d2 <= 0.f) {
-        um = u0;
-        up = u0;
-    } else if (fabsf(d2) > 2.f * fabsf(d1)) {
-        um = fmaf(-2.f, d1, u0);
-    } else if (fabsf(d1) > 2.f * fabsf(d2)) {
-        up = fmaf(2.f, d2, u0);
-    }
-    vm = um;
-    vp = up;
+    // the constraints by selects: FP32 arithmetic is cheap, divergence is not
+    const bool flat = d1 * d2 <= 0.f;
+    const bool A = fabsf(d2) > 2.f * fabsf(d1);
+    const bool Bp = !A && fabsf(d1) > 2.f * fabsf(d2);
+    const float umc = fmaf(-2.f, d1, u0), upc = fmaf(2.f, d2, u0);
+    vm = flat ? u0 : (A ? umc : um);
+    vp = flat ? u0 : (Bp ? upc : up);
 }
 
 // Point primitives: velocity, pressure (dual energy) and sound speed.
