@@ -108,37 +108,39 @@ __device__ __forceinline__ float max_nonneg(float x, float y) { return fmaxf(x, 
 // Monotonised-central slope from the two one-sided differences a = u0 - u-1
 // and b = u1 - u0: minmod((a + b)/2, 2a, 2b), zero unless a and b share a
 // strict sign.
+// The rare cases (an operand or result outside the normal range) in calls
+// of their own: a real branch, so that no warp issues their FP64 operations
+// unless one of its lanes needs them.
+static __device__ __noinline__ double mc_slope_rare(double s, int mh, unsigned int ml)
+{
+    return fmin(0.5 * fabs(s), 2.0 * from_hl(mh, ml));
+}
+
 __device__ __forceinline__ double mc_slope(double a, double b)
 {
-    const HL A = hl(a), Bv = hl(b);
-    const bool same = ((A.h ^ Bv.h) >= 0) && !is_zero(A) && !is_zero(Bv);
-    if (!same)
-        return 0.0;
+    // the common case without branches: the one FP64 operation (a + b) for
+    // every lane, the case analysis on the integer words by selects
     const double s = a + b;
-    const HL S = hl(s);
+    const HL A = hl(a), Bv = hl(b), S = hl(s);
+    const bool same = ((A.h ^ Bv.h) >= 0) && !is_zero(A) && !is_zero(Bv);
     const int ah = A.h & 0x7FFFFFFF, bh = Bv.h & 0x7FFFFFFF, sh = S.h & 0x7FFFFFFF;
     // m = min(|a|, |b|)
     const bool alb = mag_lt(ah, A.l, bh, Bv.l);
     const int mh = alb ? ah : bh;
     const unsigned int ml = alb ? A.l : Bv.l;
     const int em = mh >> 20, es = sh >> 20;
-    int rh;
-    unsigned int rl;
-    if (em >= 1 && em <= 2043 && es >= 2 && es <= 2046) {
-        // |s|/2 <= 2 m  <=>  |s| <= 4 m: compare with m's exponent raised by 2
-        if (!mag_lt(mh + (2 << 20), ml, sh, S.l)) {
-            rh = sh - (1 << 20);  // |s| / 2
-            rl = S.l;
-        } else {
-            rh = mh + (1 << 20);  // 2 m
-            rl = ml;
-        }
-    } else {
-        const HL R = hl(fmin(0.5 * fabs(s), 2.0 * from_hl(mh, ml)));
+    // |s|/2 <= 2 m  <=>  |s| <= 4 m: compare with m's exponent raised by 2
+    const bool half_s = !mag_lt(mh + (2 << 20), ml, sh, S.l);
+    int rh = half_s ? sh - (1 << 20) : mh + (1 << 20);  // |s| / 2 or 2 m
+    unsigned int rl = half_s ? S.l : ml;
+    if (__builtin_expect(same && !(em >= 1 && em <= 2043 && es >= 2 && es <= 2046), 0)) {
+        const HL R = hl(mc_slope_rare(s, mh, ml));
         rh = R.h;
         rl = R.l;
     }
-    return from_hl(rh | (A.h & (int)0x80000000), rl);
+    rh = same ? (rh | (A.h & (int)0x80000000)) : 0;
+    rl = same ? rl : 0u;
+    return from_hl(rh, rl);
 }
 __device__ __forceinline__ float mc_slope(float a, float b)
 {
@@ -149,17 +151,26 @@ __device__ __forceinline__ float mc_slope(float a, float b)
     return a * b > 0.f ? copysignf(r, s) : 0.f;
 }
 
-// x/2 and 2x exactly, on the exponent field of the high word while the
-// result stays a normal number; zero stays zero; otherwise by a multiply.
+// x/2 exactly: on the exponent field of the high word for normal results;
+// zero, infinity and NaN stay as they are; subnormal inputs or results by a
+// multiply in a call of its own.
+static __device__ __noinline__ double half_rare(double x) { return 0.5 * x; }
 __device__ __forceinline__ double half_d(double x)
 {
     const HL X = hl(x);
     const int e = (X.h >> 20) & 0x7FF;
-    if (e > 1 && e < 2047)
-        return from_hl(X.h - (1 << 20), X.l);
-    if (is_zero(X))
-        return x;
-    return 0.5 * x;
+    if (__builtin_expect(e == 1 || (e == 0 && !is_zero(X)), 0))
+        return half_rare(x);
+    return (e > 1 && e < 2047) ? from_hl(X.h - (1 << 20), X.l) : x;
+}
+
+// The CW84 constraints in FP64 for half-widths outside the normal range.
+static __device__ __noinline__ void cw84_rare(double &d1, double &d2)
+{
+    if (fabs(d2) > 2.0 * fabs(d1))
+        d2 = 2.0 * d1;
+    else if (fabs(d1) > 2.0 * fabs(d2))
+        d1 = 2.0 * d2;
 }
 
 // CW84 PPM on u_{-2..2}: limited values at the cell's two ends.  The
@@ -169,7 +180,8 @@ __device__ __forceinline__ double half_d(double x)
 // The CW84 monotonicity constraints then act on (d1, d2): flat at an
 // extremum (d1 d2 <= 0); when |d2| > 2|d1| the parabola overshoots on the
 // minus side and d2 becomes 2 d1; when |d1| > 2|d2|, d1 becomes 2 d2.
-// Finally up = u0 + d1, um = u0 - d2.
+// Finally up = u0 + d1, um = u0 - d2.  The FP64 operations run for every
+// lane; the constraints choose on the integer words.
 __device__ __forceinline__ void ppm5(double um2, double um1, double u0, double up1, double up2, double &vm,
                                      double &vp)
 {
@@ -180,27 +192,25 @@ __device__ __forceinline__ void ppm5(double um2, double um1, double u0, double u
     const double s6 = 1.0 / 6.0;
     double d1 = fma(d0 - dp, s6, half_d(ap1));
     double d2 = fma(d0 - dm, s6, half_d(am1));
-    const HL D1 = hl(d1), D2 = hl(d2);
-    if (((D1.h ^ D2.h) < 0) || is_zero(D1) || is_zero(D2)) {
-        vm = u0;
-        vp = u0;
-        return;
-    }
+    HL D1 = hl(d1), D2 = hl(d2);
+    const bool flat = ((D1.h ^ D2.h) < 0) || is_zero(D1) || is_zero(D2);
     const int h1 = D1.h & 0x7FFFFFFF, h2 = D2.h & 0x7FFFFFFF;
     const int e1 = h1 >> 20, e2 = h2 >> 20;
-    if (e1 >= 1 && e1 <= 2045 && e2 >= 1 && e2 <= 2045) {
-        if (mag_lt(h1 + (1 << 20), D1.l, h2, D2.l))          // |d2| > 2|d1|
-            d2 = from_hl(D1.h + (1 << 20), D1.l);             // 2 d1
-        else if (mag_lt(h2 + (1 << 20), D2.l, h1, D1.l))     // |d1| > 2|d2|
-            d1 = from_hl(D2.h + (1 << 20), D2.l);             // 2 d2
+    if (__builtin_expect(!flat && !(e1 >= 1 && e1 <= 2045 && e2 >= 1 && e2 <= 2045), 0)) {
+        cw84_rare(d1, d2);
+        D1 = hl(d1);
+        D2 = hl(d2);
     } else {
-        if (fabs(d2) > 2.0 * fabs(d1))
-            d2 = 2.0 * d1;
-        else if (fabs(d1) > 2.0 * fabs(d2))
-            d1 = 2.0 * d2;
+        const bool A = mag_lt(h1 + (1 << 20), D1.l, h2, D2.l);         // |d2| > 2|d1|: d2 = 2 d1
+        const bool Bp = !A && mag_lt(h2 + (1 << 20), D2.l, h1, D1.l);  // |d1| > 2|d2|: d1 = 2 d2
+        const HL N2 = {A ? D1.h + (1 << 20) : D2.h, A ? D1.l : D2.l};
+        const HL N1 = {Bp ? D2.h + (1 << 20) : D1.h, Bp ? D2.l : D1.l};
+        D1 = N1;
+        D2 = N2;
     }
-    vp = u0 + d1;
-    vm = u0 - d2;
+    // flat: both half-widths zero, so that up = um = u0
+    vp = u0 + from_hl(flat ? 0 : D1.h, flat ? 0u : D1.l);
+    vm = u0 - from_hl(flat ? 0 : D2.h, flat ? 0u : D2.l);
 }
 
 // The FP32 form: the interface values first, then the constraints on
