@@ -462,6 +462,13 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
     const T eps1 = Num<T>::from_d(A.eps1);
     const T inv_gm1 = Num<T>::from_d(A.inv_gm1);
     constexpr int RWX = TXM + 2 * NG, RWY = TYM + 2 * NG;  // staged plane shape
+    // the first line group with faces of each axis writes its face sums, the
+    // later ones add to them: no zeroing of the face accumulators is needed
+    int first_g[3] = {-1, -1, -1};
+    for (int g = NGROUPS - 1; g >= 0; g--)
+        for (int a = 0; a < 3; a++)
+            if (c_groups[g].has[a])
+                first_g[a] = g;
     bool bad = false;
 
     for (int it = blockIdx.x; it < A.n_items; it += gridDim.x) {
@@ -528,12 +535,6 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
         for (int t = 0; t < 4; t++)
             magic[t] = (unsigned)((0x100000000ULL + nlist[t] - 1) / nlist[t]);
 
-        for (int q = tid; q < nf * FXS; q += NTHREADS)
-            faccx[q] = T(0);
-        for (int q = tid; q < nf * FYS; q += NTHREADS)
-            faccy[q] = T(0);
-        for (int q = tid; q < 2 * nf * C64; q += NTHREADS)
-            zacc[q] = T(0);
         for (int kz = -3; kz <= 1; kz++)
             stage_plane(kz);
         __syncthreads();
@@ -780,10 +781,13 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                                 acc[F_SX + k] += pacc;
                         T *dst = axis == 0 ? faccx : (axis == 1 ? faccy : zacc + (kz & 1) * nf * C64);
                         const int stride = axis == 2 ? C64 : (axis == 0 ? FXS : FYS);
+                        const bool first = g == (axis == 0 ? first_g[0] : (axis == 1 ? first_g[1] : first_g[2]));
 #pragma unroll
                         for (int f = 0; f < MAXNF; f++)
-                            if (f < nf)
-                                dst[f * stride + fslot] += acc[f];
+                            if (f < nf) {
+                                T *o = dst + f * stride + fslot;
+                                *o = first ? acc[f] : *o + acc[f];
+                            }
                     }
                     if (axis == 2 && act && kz < E) {
                         // leave this plane's +z ends (values and primitives) for the next plane
@@ -801,21 +805,33 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                 }
                 __syncthreads();
             }
-            // ---- finish the divergence of plane kz-1 (its upper z face is done) ----
-            if (kz >= 1) {
-                const T *zp = zacc + (kz & 1) * nf * C64;
-                const T *zm = zacc + ((kz - 1) & 1) * nf * C64;
-                for (int q = tid; q < nf * ncin; q += NTHREADS) {
-                    int f = q / ncin, c = q - f * ncin;
-                    int i = c % tx, j = c / tx;
+            // ---- plane end, one pass: the divergence of plane kz-1 (its upper z
+            // face is done) and the in-plane part of plane kz's, by the same
+            // thread for each (field, cell), so dxy is read before it is
+            // rewritten; then the next plane is staged ----
+            for (int q = tid; q < nf * ncin; q += NTHREADS) {
+                int f = q / ncin, c = q - f * ncin;
+                int i = c % tx, j = c / tx;
+                if (kz >= 1) {
+                    const T *zp = zacc + (kz & 1) * nf * C64;
+                    const T *zm = zacc + ((kz - 1) & 1) * nf * C64;
                     double dz = Num<T>::to_d(zp[f * C64 + c]) - Num<T>::to_d(zm[f * C64 + c]);
                     double d = -(dxy[f * C64 + c] + dz) * rdx;
                     dUb[(long long)f * E * E * E + (long long)(kz - 1) * E * E + (long long)(y0 + j) * E + (x0 + i)] = d;
                 }
+                if (inplane) {
+                    const T *fx = faccx + f * FXS;
+                    const T *fy = faccy + f * FYS;
+                    double dX = Num<T>::to_d(fx[j * (tx + 1) + i + 1]) - Num<T>::to_d(fx[j * (tx + 1) + i]);
+                    double dY = Num<T>::to_d(fy[(j + 1) * tx + i]) - Num<T>::to_d(fy[j * tx + i]);
+                    dxy[f * C64 + c] = dX + dY;
+                }
+            }
+            {
                 double *fb;
-                if (A.faces != nullptr && (kz == 1 || kz == E) && (fb = face_block()) != nullptr) {
+                if (kz >= 1 && A.faces != nullptr && (kz == 1 || kz == E) && (fb = face_block()) != nullptr) {
                     // the subgrid's -z (below plane 0) or +z (above plane E-1) face
-                    const T *zs = kz == 1 ? zm : zp;
+                    const T *zs = zacc + ((kz == 1 ? kz - 1 : kz) & 1) * nf * C64;
                     double *o = fb + (long long)(kz == 1 ? 4 : 5) * nf * E * E;
                     for (int q = tid; q < nf * ncin; q += NTHREADS) {
                         int f = q / ncin, c = q - f * ncin;
@@ -823,25 +839,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                         o[(long long)f * E * E + (y0 + j) * E + (x0 + i)] = Num<T>::to_d(zs[f * C64 + c]);
                     }
                 }
-            }
-            __syncthreads();
-            if (kz >= 1) {
-                T *zm = zacc + ((kz - 1) & 1) * nf * C64;
-                for (int q = tid; q < nf * C64; q += NTHREADS)
-                    zm[q] = T(0);
-            }
-            if (inplane) {
-                for (int q = tid; q < nf * ncin; q += NTHREADS) {
-                    int f = q / ncin, c = q - f * ncin;
-                    int i = c % tx, j = c / tx;
-                    const T *fx = faccx + f * FXS;
-                    const T *fy = faccy + f * FYS;
-                    double dX = Num<T>::to_d(fx[j * (tx + 1) + i + 1]) - Num<T>::to_d(fx[j * (tx + 1) + i]);
-                    double dY = Num<T>::to_d(fy[(j + 1) * tx + i]) - Num<T>::to_d(fy[j * tx + i]);
-                    dxy[f * C64 + c] = dX + dY;
-                }
-                double *fb;
-                if (A.faces != nullptr && (x0 == 0 || y0 == 0 || x0 + tx == E || y0 + ty == E) &&
+                if (inplane && A.faces != nullptr && (x0 == 0 || y0 == 0 || x0 + tx == E || y0 + ty == E) &&
                     (fb = face_block()) != nullptr) {
                     // x and y faces of plane kz on the subgrid's boundary
                     const long long EE = (long long)E * E;
@@ -866,13 +864,6 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                                 fb[3 * nf * EE + o] = Num<T>::to_d(fy[ty * tx + i]);
                         }
                 }
-            }
-            __syncthreads();
-            if (inplane) {
-                for (int q = tid; q < nf * FXS; q += NTHREADS)
-                    faccx[q] = T(0);
-                for (int q = tid; q < nf * FYS; q += NTHREADS)
-                    faccy[q] = T(0);
             }
             if (kz + 3 <= E + 2)
                 stage_plane(kz + 3);
