@@ -2,6 +2,7 @@
 // handle, validation, work list, launches, the RK3 CUDA graph and the
 // autotuner.  The kernels live in rhs_kernel.cuh and step_kernels.cuh.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -18,6 +19,16 @@
 #include "oct_common.cuh"
 #include "rhs_launch.h"
 #include "step_kernels.cuh"
+
+namespace {
+// An NVTX range around each ABI call that launches work, so that timelines
+// (nsys, ncu --nvtx) show which call a kernel belongs to.  Without a tool
+// attached NVTX calls cost a pointer test.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 using namespace octh;
 
@@ -358,6 +369,7 @@ extern "C" oct_status oct_hydro_set_reconstruction(oct_hydro_t h, int variables)
 extern "C" oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, const int32_t *origin, int root_cells,
                                         int periodic)
 {
+    NvtxRange nvtx_range("oct_hydro_set_amr");
     if (!h)
         return fail(OCT_E_ARG, "handle is NULL");
     if (!h->layout_ok)
@@ -653,6 +665,7 @@ static oct_status ensure_scratch(oct_hydro *h)
 
 extern "C" oct_status oct_hydro_rhs(oct_hydro_t h, const double *U, double *dUdt, double *amax, void *cuda_stream)
 {
+    NvtxRange nvtx_range("oct_hydro_rhs");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
         return st;
@@ -682,6 +695,7 @@ static oct_status launch_dt(oct_hydro *h, cudaStream_t s)
 
 extern "C" oct_status oct_hydro_max_dt(oct_hydro_t h, const double *U, double *dt_host_out, void *cuda_stream)
 {
+    NvtxRange nvtx_range("oct_hydro_max_dt");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
         return st;
@@ -721,6 +735,7 @@ static oct_status launch_ghosts(oct_hydro *h, double *U, cudaStream_t s)
 
 extern "C" oct_status oct_hydro_fill_ghosts(oct_hydro_t h, double *U, void *cuda_stream)
 {
+    NvtxRange nvtx_range("oct_hydro_fill_ghosts");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
         return st;
@@ -775,6 +790,7 @@ static oct_status enqueue_step(oct_hydro *h, double *U, cudaStream_t s)
 
 extern "C" oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_used_host_out, void *cuda_stream)
 {
+    NvtxRange nvtx_range("oct_hydro_rk_step");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
         return st;
@@ -815,6 +831,7 @@ extern "C" oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_use
 extern "C" oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int n_steps, double *dt_last_out,
                                               void *cuda_stream)
 {
+    NvtxRange nvtx_range("oct_hydro_rk_steps_host");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
         return st;
@@ -839,6 +856,7 @@ extern "C" oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int
 
 extern "C" oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_host, void *cuda_stream)
 {
+    NvtxRange nvtx_range("oct_hydro_rhs_host");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
         return st;
@@ -859,6 +877,7 @@ extern "C" oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, do
 
 extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, void *cuda_stream)
 {
+    NvtxRange nvtx_range("oct_hydro_autotune");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
         return st;
@@ -1048,6 +1067,7 @@ extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_s
                                                double cfl, double de_switch1, const double *U, const double *dx,
                                                double *dUdt, double *dt, void *cuda_stream)
 {
+    NvtxRange nvtx_range("oct_hydro_rhs_dt_noalloc");
     if (n_subgrids <= 0 || n_subgrids > NA_MAX_SUB)
         return fail(OCT_E_ARG,
                     "n_subgrids must be in 1..%d, the size of the static scratch of the allocation-free call "
