@@ -201,7 +201,11 @@ oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_
 /* Times the candidate launch shapes of the RHS kernel on U_sample -- tile
  * capacity (8x8 or 8x4 cells per work item) x resident CTAs per SM (1 up to
  * the occupancy limit) -- and keeps the fastest for this layout, precision
- * and reconstruction choice.  Drops captured graphs. */
+ * and reconstruction choice.  Drops captured graphs.  When the environment
+ * variable OCT_HYDRO_TUNE_CACHE names a file, a result stored there for the
+ * same GPU model, SM count, form, field count and edge counts is applied
+ * without trial launches, and a new result is appended (one text line per
+ * result; a file that cannot be read or written only disables the cache). */
 oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, void *cuda_stream);
 
 /* Allocation-free RHS + CFL dt (the paper has no counterpart: this is a

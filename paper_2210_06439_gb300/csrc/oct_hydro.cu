@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -875,6 +876,63 @@ extern "C" oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, do
     return OCT_OK;
 }
 
+// Autotuner cache (optional): when the environment variable
+// OCT_HYDRO_TUNE_CACHE names a file, a tuning result is looked up there
+// before any trial launch and appended after one.  One line per result:
+// "<key> <tile mode> <CTAs per SM>", the key made of the GPU name, its SM
+// count, the form (precision, reconstruction), the field count and the
+// batch's edge counts, e.g. "NVIDIA_GB300|152|f0|nf11|e8x512 1 2".
+static std::mutex g_tune_mutex;
+
+static std::string tune_key(const oct_hydro *h)
+{
+    cudaDeviceProp prop;
+    std::string name = cudaGetDeviceProperties(&prop, h->device) == cudaSuccess ? prop.name : "gpu";
+    for (char &c : name)
+        if (c == ' ' || c == '|')
+            c = '_';
+    int n8 = 0, n12 = 0, n16 = 0;
+    for (int E : h->edge)
+        (E == 8 ? n8 : (E == 12 ? n12 : n16))++;
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|%d|f%d|nf%d|e8x%d,e12x%d,e16x%d", name.c_str(), h->n_sm, h->precision + 2 * h->recon,
+             h->nf, n8, n12, n16);
+    return buf;
+}
+
+static bool tune_lookup(const std::string &key, int *mode, int *use)
+{
+    const char *path = getenv("OCT_HYDRO_TUNE_CACHE");
+    if (!path || !*path)
+        return false;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    FILE *f = fopen(path, "r");
+    if (!f)
+        return false;
+    char k[256];
+    int m, u;
+    bool found = false;
+    while (fscanf(f, "%255s %d %d", k, &m, &u) == 3)
+        if (key == k && (m == 0 || m == 1) && u >= 1) {
+            *mode = m, *use = u, found = true;  // the last entry for a key wins
+        }
+    fclose(f);
+    return found;
+}
+
+static void tune_store(const std::string &key, int mode, int use)
+{
+    const char *path = getenv("OCT_HYDRO_TUNE_CACHE");
+    if (!path || !*path)
+        return;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    FILE *f = fopen(path, "a");
+    if (!f)
+        return;  // a cache that cannot be written is not an error
+    fprintf(f, "%s %d %d\n", key.c_str(), mode, use);
+    fclose(f);
+}
+
 extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, void *cuda_stream)
 {
     NvtxRange nvtx_range("oct_hydro_autotune");
@@ -885,6 +943,17 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
         return st;
     if ((st = ensure_scratch(h)) != OCT_OK)
         return st;
+    const std::string key = tune_key(h);
+    {
+        int mode, use;
+        if (tune_lookup(key, &mode, &use) && use <= h->ctas_per_sm[form_of(h)][mode]) {
+            h->tile_mode = mode;
+            h->cta_use[form_of(h)][mode] = use;
+            build_items(h);
+            drop_graphs(h);
+            return upload_items(h);
+        }
+    }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
@@ -925,6 +994,7 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
     cudaEventDestroy(e1);
     h->tile_mode = best_mode;
     h->cta_use[prec][best_mode] = best_use;
+    tune_store(key, best_mode, best_use);
     build_items(h);
     drop_graphs(h);
     return upload_items(h);
