@@ -154,7 +154,9 @@ oct_status oct_hydro_set_params(oct_hydro_t h, int precision, double cfl, double
                                 double de_switch2);
 
 /* Caps dt in oct_hydro_rk_step (dt_cap > 0), e.g. to land on an output time;
- * dt_cap <= 0 removes the cap. */
+ * dt_cap <= 0 removes the cap.  Waits for the device to be idle (so that no
+ * step in flight sees the change), then stores the cap in device memory,
+ * where the captured step graphs read it: changing it costs no recapture. */
 oct_status oct_hydro_set_dt_cap(oct_hydro_t h, double dt_cap);
 
 /* Number of doubles of the state array the layout spans, and of dUdt. */
@@ -184,7 +186,8 @@ oct_status oct_hydro_fill_ghosts(oct_hydro_t h, double *U, void *cuda_stream);
  * floors and dual-energy re-synchronisation, and a ghost fill after each
  * stage (unless OCT_BC_GIVEN; across levels, with the flux correction in
  * each RHS, after oct_hydro_set_amr).  On entry U's ghosts must be valid.  The
- * sequence is replayed from a CUDA graph captured on first use for this U.
+ * sequence is replayed from a CUDA graph captured on first use for this U (on
+ * a non-default stream; up to 16 state pointers are remembered).
  * When dt_used_host_out is not NULL the stream is synchronised and the dt
  * used is written there. */
 oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_used_host_out, void *cuda_stream);

@@ -89,6 +89,7 @@ struct oct_hydro {
     long long *d_off = nullptr, *d_doff = nullptr, *d_cell_begin = nullptr;
     double *d_dx = nullptr;
     WorkItem *d_items = nullptr;
+    double *d_dtcap = nullptr;  // dt cap of oct_hydro_rk_step (0: none), read by the captured graph
     double *d_amax_tile = nullptr, *d_dt = nullptr, *d_W = nullptr, *d_L = nullptr, *d_Uhost = nullptr,
            *d_Lhost = nullptr;
     unsigned *d_flags = nullptr;
@@ -237,6 +238,10 @@ extern "C" oct_status oct_hydro_create(int n_subgrids, int edge, int ghost, int 
         st = fail(OCT_E_CUDA, "cudaMemset flags");
     if (st == OCT_OK && cudaMalloc(&h->d_dt, sizeof(double)) != cudaSuccess)
         st = fail(OCT_E_NOMEM, "cudaMalloc dt");
+    if (st == OCT_OK && cudaMalloc(&h->d_dtcap, sizeof(double)) != cudaSuccess)
+        st = fail(OCT_E_NOMEM, "cudaMalloc dt cap");
+    if (st == OCT_OK && cudaMemset(h->d_dtcap, 0, sizeof(double)) != cudaSuccess)
+        st = fail(OCT_E_CUDA, "cudaMemset dt cap");
     if (st != OCT_OK) {
         oct_hydro_destroy(h);
         return st;
@@ -580,8 +585,11 @@ extern "C" oct_status oct_hydro_set_dt_cap(oct_hydro_t h, double dt_cap)
         return fail(OCT_E_ARG, "handle is NULL");
     if (std::isnan(dt_cap))
         return fail(OCT_E_ARG, "dt_cap is NaN");
+    // the captured step graphs read the cap from device memory; wait for any
+    // step in flight before changing it
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(h->d_dtcap, &dt_cap, sizeof(double), cudaMemcpyHostToDevice));
     h->dt_cap = dt_cap;
-    drop_graphs(h);
     return OCT_OK;
 }
 
@@ -686,10 +694,10 @@ extern "C" oct_status oct_hydro_rhs(oct_hydro_t h, const double *U, double *dUdt
     return OCT_OK;
 }
 
-static oct_status launch_dt(oct_hydro *h, cudaStream_t s)
+static oct_status launch_dt(oct_hydro *h, cudaStream_t s, bool capped = true)
 {
-    dt_kernel<<<1, 1024, 0, s>>>((int)h->items.size(), h->d_items, h->d_dx, h->d_amax_tile, h->cfl, h->dt_cap,
-                                 h->d_dt);
+    dt_kernel<<<1, 1024, 0, s>>>((int)h->items.size(), h->d_items, h->d_dx, h->d_amax_tile, h->cfl,
+                                 capped ? h->d_dtcap : nullptr, h->d_dt);
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;
 }
@@ -709,10 +717,7 @@ extern "C" oct_status oct_hydro_max_dt(oct_hydro_t h, const double *U, double *d
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if ((st = launch_rhs(h, U, h->d_L, s)) != OCT_OK)
         return st;
-    double cap = h->dt_cap;
-    h->dt_cap = 0.0;
-    st = launch_dt(h, s);
-    h->dt_cap = cap;
+    st = launch_dt(h, s, false);
     if (st != OCT_OK)
         return st;
     CUDA_TRY(cudaMemcpyAsync(dt_host_out, h->d_dt, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -800,6 +805,8 @@ extern "C" oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_use
     if ((st = ensure_scratch(h)) != OCT_OK)
         return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (h->graphs.size() >= 16 && !h->graphs.count(U))
+        drop_graphs(h);  // bound the per-state-pointer graph cache
     GraphEntry &ge = h->graphs[U];
     if (!ge.exec && s != 0) {
         cudaGraph_t graph;
@@ -1039,6 +1046,7 @@ extern "C" void oct_hydro_destroy(oct_hydro_t h)
     free_layout(h);
     dfree(h->d_flags);
     dfree(h->d_dt);
+    dfree(h->d_dtcap);
     delete h;
 }
 
@@ -1208,7 +1216,7 @@ extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_s
     A.face_slot = nullptr;
     int grid = std::min(n_items, D->n_sm * D->ctas[precision]);
     CUDA_TRY(rhs_launch(precision, 0, grid, s, A));
-    dt_kernel<<<1, 1024, 0, s>>>(n_items, d_items, dx, d_amax, cfl, 0.0, dt);
+    dt_kernel<<<1, 1024, 0, s>>>(n_items, d_items, dx, d_amax, cfl, nullptr, dt);
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;
 }

@@ -22,8 +22,11 @@ __global__ void amax_subgrid_kernel(int n_sub, const int *item_begin, const doub
 // dt = cfl * min over items of dx_s / a_max,item (Sec. V-A, time-step size);
 // min_t dx/a_t = dx / max_t a_t exactly because correctly rounded division is
 // monotone.  One block of 1024 threads; writes dt[0].
+// dt = cfl * min over work items of dx / a_max, capped by *dt_cap when
+// dt_cap is not null and *dt_cap > 0 (the cap lives in device memory so that a
+// captured step graph follows later changes of it).
 __global__ void dt_kernel(int n_items, const WorkItem *items, const double *dx, const double *amax_tile, double cfl,
-                          double dt_cap, double *dt)
+                          const double *dt_cap, double *dt)
 {
     __shared__ double red[32];
     double m = INFINITY;
@@ -40,8 +43,9 @@ __global__ void dt_kernel(int n_items, const WorkItem *items, const double *dx, 
             m = fmin(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
         if (threadIdx.x == 0) {
             double d = cfl * m;
-            if (dt_cap > 0.0 && dt_cap < d)
-                d = dt_cap;
+            const double cap = dt_cap ? *dt_cap : 0.0;
+            if (cap > 0.0 && cap < d)
+                d = cap;
             dt[0] = d;
         }
     }

@@ -208,3 +208,22 @@ def test_rk3_step_with_floor_firings_matches_oracle(precision):
     errs = field_errors(interior_layout(got, p), interior_layout(ref.U, p), p.nf, e3s(p))
     assert np.all(errs <= (1e-12 if precision == 0 else 1e-6)), errs
     assert np.all(interior_layout(got, p).reshape(p.n_sub, p.nf, -1)[:, 6:] >= 0.0)
+
+
+def test_dt_cap_applies_to_replayed_graphs():
+    """The cap lives in device memory: a captured step follows later changes
+    of it, and removing it restores the CFL step of max_dt."""
+    torch = _torch()
+    p = oracle_filled(inputs.periodic_box(nsub=2))
+    H = _hydro(p)
+    st = torch.cuda.Stream()
+    U = torch.from_numpy(p.U).cuda()
+    dt_free = H.max_dt(U, stream=st)
+    H.set_dt_cap(dt_free / 4)
+    assert H.rk_step(U, stream=st) == dt_free / 4
+    H.set_dt_cap(dt_free / 8)
+    assert H.rk_step(U, stream=st) == dt_free / 8
+    H.set_dt_cap(0.0)
+    dt_now = H.max_dt(U, stream=st)
+    assert H.rk_step(U, stream=st) == dt_now
+    assert H.error_flags() == 0
