@@ -53,6 +53,11 @@
  * (oct_hydro_max_dt, oct_hydro_rk_step with a non-NULL dt pointer,
  * oct_hydro_get_error_flags, the *_host calls) synchronise that stream.
  * A handle is not thread-safe: one host thread at a time per handle.
+ *
+ * Device: a handle belongs to the device that is current at
+ * oct_hydro_create; every call on it makes that device current for its
+ * duration and restores the caller's device afterwards.  Streams and
+ * pointers passed in must belong to that device.
  */
 #ifndef OCT_HYDRO_H
 #define OCT_HYDRO_H

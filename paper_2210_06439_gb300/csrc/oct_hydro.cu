@@ -110,6 +110,23 @@ static void dfree(P *&p)
     p = nullptr;
 }
 
+// Makes the handle's device current for the duration of an ABI call and
+// restores the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(const oct_hydro *h)
+    {
+        int cur = -1;
+        if (h && cudaGetDevice(&cur) == cudaSuccess && cur != h->device && cudaSetDevice(h->device) == cudaSuccess)
+            prev = cur;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
 static void drop_graphs(oct_hydro *h)
 {
     for (auto &kv : h->graphs)
@@ -263,6 +280,7 @@ extern "C" oct_status oct_hydro_create(int n_subgrids, int edge, int ghost, int 
 extern "C" oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, const int64_t *offsets,
                                            const double *dx, const int32_t *level, const int32_t *neighbours, int bc)
 {
+    DeviceGuard device_guard(h);
     (void)level;
     if (!h)
         return fail(OCT_E_ARG, "handle is NULL");
@@ -361,6 +379,7 @@ extern "C" oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, 
 
 extern "C" oct_status oct_hydro_set_reconstruction(oct_hydro_t h, int variables)
 {
+    DeviceGuard device_guard(h);
     if (!h)
         return fail(OCT_E_ARG, "handle is NULL");
     if (variables != OCT_RECON_CONSERVED && variables != OCT_RECON_PRIMITIVE)
@@ -375,6 +394,7 @@ extern "C" oct_status oct_hydro_set_reconstruction(oct_hydro_t h, int variables)
 extern "C" oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, const int32_t *origin, int root_cells,
                                         int periodic)
 {
+    DeviceGuard device_guard(h);
     NvtxRange nvtx_range("oct_hydro_set_amr");
     if (!h)
         return fail(OCT_E_ARG, "handle is NULL");
@@ -560,6 +580,7 @@ extern "C" oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, con
 extern "C" oct_status oct_hydro_set_params(oct_hydro_t h, int precision, double cfl, double rho_floor,
                                            double de_switch1, double de_switch2)
 {
+    DeviceGuard device_guard(h);
     if (!h)
         return fail(OCT_E_ARG, "handle is NULL");
     if (precision != OCT_FP64 && precision != OCT_MIXED)
@@ -581,6 +602,7 @@ extern "C" oct_status oct_hydro_set_params(oct_hydro_t h, int precision, double 
 
 extern "C" oct_status oct_hydro_set_dt_cap(oct_hydro_t h, double dt_cap)
 {
+    DeviceGuard device_guard(h);
     if (!h)
         return fail(OCT_E_ARG, "handle is NULL");
     if (std::isnan(dt_cap))
@@ -595,11 +617,13 @@ extern "C" oct_status oct_hydro_set_dt_cap(oct_hydro_t h, double dt_cap)
 
 extern "C" int64_t oct_hydro_state_len(oct_hydro_t h)
 {
+    DeviceGuard device_guard(h);
     return h && h->layout_ok ? h->state_len : -1;
 }
 
 extern "C" int64_t oct_hydro_rhs_len(oct_hydro_t h)
 {
+    DeviceGuard device_guard(h);
     return h && h->layout_ok ? h->rhs_len : -1;
 }
 
@@ -674,6 +698,7 @@ static oct_status ensure_scratch(oct_hydro *h)
 
 extern "C" oct_status oct_hydro_rhs(oct_hydro_t h, const double *U, double *dUdt, double *amax, void *cuda_stream)
 {
+    DeviceGuard device_guard(h);
     NvtxRange nvtx_range("oct_hydro_rhs");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
@@ -704,6 +729,7 @@ static oct_status launch_dt(oct_hydro *h, cudaStream_t s, bool capped = true)
 
 extern "C" oct_status oct_hydro_max_dt(oct_hydro_t h, const double *U, double *dt_host_out, void *cuda_stream)
 {
+    DeviceGuard device_guard(h);
     NvtxRange nvtx_range("oct_hydro_max_dt");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
@@ -741,6 +767,7 @@ static oct_status launch_ghosts(oct_hydro *h, double *U, cudaStream_t s)
 
 extern "C" oct_status oct_hydro_fill_ghosts(oct_hydro_t h, double *U, void *cuda_stream)
 {
+    DeviceGuard device_guard(h);
     NvtxRange nvtx_range("oct_hydro_fill_ghosts");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
@@ -796,6 +823,7 @@ static oct_status enqueue_step(oct_hydro *h, double *U, cudaStream_t s)
 
 extern "C" oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_used_host_out, void *cuda_stream)
 {
+    DeviceGuard device_guard(h);
     NvtxRange nvtx_range("oct_hydro_rk_step");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
@@ -839,6 +867,7 @@ extern "C" oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_use
 extern "C" oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int n_steps, double *dt_last_out,
                                               void *cuda_stream)
 {
+    DeviceGuard device_guard(h);
     NvtxRange nvtx_range("oct_hydro_rk_steps_host");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
@@ -864,6 +893,7 @@ extern "C" oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int
 
 extern "C" oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_host, void *cuda_stream)
 {
+    DeviceGuard device_guard(h);
     NvtxRange nvtx_range("oct_hydro_rhs_host");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
@@ -942,6 +972,7 @@ static void tune_store(const std::string &key, int mode, int use)
 
 extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, void *cuda_stream)
 {
+    DeviceGuard device_guard(h);
     NvtxRange nvtx_range("oct_hydro_autotune");
     oct_status st = check_ready(h);
     if (st != OCT_OK)
@@ -1009,6 +1040,7 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
 
 extern "C" oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *ctas_per_sm, int *n_items)
 {
+    DeviceGuard device_guard(h);
     oct_status st = check_ready(h);
     if (st != OCT_OK)
         return st;
@@ -1025,6 +1057,7 @@ extern "C" oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *
 
 extern "C" oct_status oct_hydro_get_error_flags(oct_hydro_t h, uint32_t *flags)
 {
+    DeviceGuard device_guard(h);
     if (!h || !flags)
         return fail(OCT_E_ARG, "handle or flags is NULL");
     unsigned v = 0;
@@ -1041,6 +1074,7 @@ extern "C" const char *oct_hydro_last_error(void)
 
 extern "C" void oct_hydro_destroy(oct_hydro_t h)
 {
+    DeviceGuard device_guard(h);
     if (!h)
         return;
     free_layout(h);
