@@ -44,6 +44,9 @@ WORKLOADS = {
                         lambda inp: inp.binary_star(4)),
     "binary_star_256": ("32768 subgrids of 8^3 (256^3 outflow box), the binary-star law, 5 species",
                         lambda inp: inp.binary_star(32), lambda inp: inp.binary_star(4)),
+    "sedov_64": ("512 subgrids of 8^3 (64^3 outflow box), Sedov-Taylor point explosion (E = 1 in the cells within "
+                 "2 cells of the centre, rho = 1, p = 1e-5 elsewhere), 1 species",
+                 lambda inp: inp.sedov_blast(nsub=8), lambda inp: inp.sedov_blast(nsub=2)),
     "amr_box_64": ("568 subgrids of 8^3 on 2 levels: a periodic 64^3 box of level-0 subgrids whose central 16^3 "
                    "cells are refined into 64 level-1 subgrids; ghost fill across levels and flux correction at "
                    "coarse-fine faces; the periodic_box law, 5 species, seed 1006",
