@@ -186,6 +186,14 @@ __device__ __forceinline__ void ppm5(double um2, double um1, double u0, double u
                                      double &vp)
 {
     const double am2 = um1 - um2, am1 = u0 - um1, ap1 = up1 - u0, ap2 = up2 - up1;
+    // a constant stencil (uniform regions such as an atmosphere) is its own
+    // reconstruction: a branch, so that warps with no other lanes skip the rest
+    const HL A2 = hl(am2), A1 = hl(am1), P1 = hl(ap1), P2 = hl(ap2);
+    if (is_zero(A2) && is_zero(A1) && is_zero(P1) && is_zero(P2)) {
+        vm = u0;
+        vp = u0;
+        return;
+    }
     const double dm = mc_slope(am2, am1);
     const double d0 = mc_slope(am1, ap1);
     const double dp = mc_slope(ap1, ap2);
