@@ -419,7 +419,30 @@ def cpu_baseline(workload, reps=1):
     t = min(ts)
     return {"value": cells / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"one SSP-RK3 step of {nsub} subgrids ({cells} cells) of the {workload} law, best of {reps}, "
-                      "FP64 C oracle (gcc -O2, OpenMP over subgrids)"}
+                      "FP64 C oracle (gcc -O2, OpenMP over subgrids)",
+            "single_thread": _oracle_rhs_single_thread(workload)}
+
+
+def _oracle_rhs_single_thread(workload, n_sub=32):
+    """The oracle's RHS on one host thread, on the first n_sub subgrids of the
+    workload's oracle sample with their ghosts filled (a bounded sample)."""
+    import oracle
+    from paper_2210_06439_gb300 import inputs
+    p = WORKLOADS[workload][2](inputs)
+    if p.bc == 3:
+        m = p.meta
+        oracle.amr_ghost_fill(int(p.edge[0]), p.off, p.nf, m["level"], m["origin"], m["n0"], m["periodic"], p.U)
+    elif p.bc != 0:
+        oracle.ghost_fill(int(p.edge[0]), p.off, p.nf, p.nbr, p.U)
+    k = min(n_sub, p.n_sub)
+    cells = int(sum(int(E) ** 3 for E in p.edge[:k]))
+    n_threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.rhs(p.edge[:k], p.off[:k], p.dx[:k], p.nf, p.U, gamma=p.gamma, nthreads=1)
+    t = time.perf_counter() - t0
+    oracle.rhs(p.edge[:0], p.off[:0], p.dx[:0], p.nf, p.U, nthreads=n_threads)  # restore the thread count
+    return {"value": cells / t, "unit": "RHS cell-updates/s", "cores": 1,
+            "sample": f"one RHS of the first {k} subgrids ({cells} cells) of the {workload} law, one thread"}
 
 
 def run_reference(args):
