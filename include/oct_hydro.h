@@ -207,8 +207,8 @@ oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int n_steps, d
 oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_host, void *cuda_stream);
 
 /* Times the candidate launch shapes of the RHS kernel on U_sample -- tile
- * capacity (8x8 or 8x4 cells per work item) x resident CTAs per SM (1 up to
- * the occupancy limit) -- and keeps the fastest for this layout, precision
+ * capacity and threads (8x8 cells per work item with 256 or 512 threads, or
+ * 8x4 with 256) x resident CTAs per SM (1 up to the occupancy limit) -- and keeps the fastest for this layout, precision
  * and reconstruction choice.  Drops captured graphs.  When the environment
  * variable OCT_HYDRO_TUNE_CACHE names a file, a result stored there for the
  * same GPU model, SM count, form, field count and edge counts is applied
@@ -246,8 +246,9 @@ oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_species, dou
 
 /* Launch shape of the RHS kernel for the current layout and precision
  * (the paper's Sec. V-B splits big kernels into tasks for the same reason:
- * enough independent work per core): tile mode (0: 8x8-cell columns, 1:
- * 8x4), CTAs resident per SM, and work items.  Any pointer may be NULL. */
+ * enough independent work per core): tile mode (0: 8x8-cell columns with
+ * 256 threads, 1: 8x4 with 256, 2: 8x8 with 512), CTAs resident per SM, and
+ * work items.  Any pointer may be NULL. */
 oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *ctas_per_sm, int *n_items);
 
 /* Reads and clears the device error flags (OCT_FLAG_*); synchronises. */

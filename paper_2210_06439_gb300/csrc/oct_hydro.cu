@@ -78,10 +78,12 @@ struct oct_hydro {
     std::vector<int> item_begin;
     std::vector<long long> cell_begin;  // packed interior-cell offset of each subgrid
     long long state_len = 0, rhs_len = 0;
-    int tile_mode = 0;       // 0: 8x8 tiles (6x6 for edge 12); 1: 8x4 tiles (6x4 for edge 12)
+    // launch shape: 0 8x8 tiles (6x6 for edge 12), 256 threads; 1 8x4 tiles (6x4
+    // for edge 12), 256 threads; 2 8x8 tiles, 512 threads
+    int tile_mode = 0;
     // [form][tile mode], form = precision + 2 * recon
-    int ctas_per_sm[4][2] = {};  // the occupancy limit
-    int cta_use[4][2] = {};      // resident CTAs per SM of the persistent grid (0: the limit)
+    int ctas_per_sm[4][RHS_MODES] = {};  // the occupancy limit (0: the shape does not fit)
+    int cta_use[4][RHS_MODES] = {};      // resident CTAs per SM of the persistent grid (0: the limit)
     int recon = OCT_RECON_CONSERVED;
     double *d_Wprim = nullptr;   // primitive variables of the state (primitive reconstruction)
     // device memory
@@ -163,14 +165,16 @@ static void free_layout(oct_hydro *h)
 static oct_status set_kernel_attrs(oct_hydro *h)
 {
     for (int form = 0; form < 4; form++)
-        for (int mode = 0; mode < 2; mode++) {
+        for (int mode = 0; mode < RHS_MODES; mode++) {
             int nb = 0;
             CUDA_TRY(rhs_prepare(form, mode, h->nf, &nb));
-            if (nb < 1)
-                return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM (%zu bytes shared memory)",
-                            rhs_smem_bytes(h->nf, form, mode));
             h->ctas_per_sm[form][mode] = nb;
         }
+    // the default 8x8 / 256-thread shape must fit
+    for (int form = 0; form < 4; form++)
+        if (h->ctas_per_sm[form][0] < 1)
+            return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM (%zu bytes shared memory)",
+                        rhs_smem_bytes(h->nf, form, 0));
     return OCT_OK;
 }
 
@@ -184,7 +188,7 @@ static void build_items(oct_hydro *h)
         h->item_begin[s] = (int)h->items.size();
         int E = h->edge[s];
         int tx = (E == 12) ? 6 : 8;
-        int ty = (h->tile_mode == 1) ? 4 : tx;
+        int ty = (h->tile_mode == 1) ? 4 : tx;  // modes 0 and 2 share the 8x8 tiles
         for (int y0 = 0; y0 < E; y0 += ty)
             for (int x0 = 0; x0 < E; x0 += tx) {
                 WorkItem w;
@@ -950,7 +954,7 @@ static bool tune_lookup(const std::string &key, int *mode, int *use)
     int m, u;
     bool found = false;
     while (fscanf(f, "%255s %d %d", k, &m, &u) == 3)
-        if (key == k && (m == 0 || m == 1) && u >= 1) {
+        if (key == k && m >= 0 && m < RHS_MODES && u >= 1) {
             *mode = m, *use = u, found = true;  // the last entry for a key wins
         }
     fclose(f);
@@ -984,7 +988,7 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
     const std::string key = tune_key(h);
     {
         int mode, use;
-        if (tune_lookup(key, &mode, &use) && use <= h->ctas_per_sm[form_of(h)][mode]) {
+        if (tune_lookup(key, &mode, &use) && mode < RHS_MODES && use <= h->ctas_per_sm[form_of(h)][mode]) {
             h->tile_mode = mode;
             h->cta_use[form_of(h)][mode] = use;
             build_items(h);
@@ -1001,7 +1005,9 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
     float best = 1e30f;
     const int prec = form_of(h);
     int best_mode = h->tile_mode, best_use = h->cta_use[prec][h->tile_mode];
-    for (int mode = 0; mode < 2; mode++) {
+    for (int mode = 0; mode < RHS_MODES; mode++) {
+        if (h->ctas_per_sm[prec][mode] < 1)
+            continue;  // this launch shape does not fit with this field count
         h->tile_mode = mode;
         build_items(h);
         if ((st = upload_items(h)) != OCT_OK)

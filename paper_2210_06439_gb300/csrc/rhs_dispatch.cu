@@ -88,44 +88,50 @@ bool build_group_tables(GroupTab *gs)
     cudaError_t rhs_launch_##NAME(int grid, cudaStream_t stream, const RhsArgs &args);
 OCT_DECLARE(fp64_m0)
 OCT_DECLARE(fp64_m1)
+OCT_DECLARE(fp64_m2)
 OCT_DECLARE(mixed_m0)
 OCT_DECLARE(mixed_m1)
+OCT_DECLARE(mixed_m2)
 OCT_DECLARE(fp64_m0_prim)
 OCT_DECLARE(fp64_m1_prim)
+OCT_DECLARE(fp64_m2_prim)
 OCT_DECLARE(mixed_m0_prim)
 OCT_DECLARE(mixed_m1_prim)
+OCT_DECLARE(mixed_m2_prim)
 #undef OCT_DECLARE
 
 namespace {
 using prepare_fn = cudaError_t (*)(int, int *);
 using launch_fn = cudaError_t (*)(int, cudaStream_t, const RhsArgs &);
 // [form][mode]; form = precision + 2 * (primitive reconstruction)
-const prepare_fn k_prepare[4][2] = {{rhs_prepare_fp64_m0, rhs_prepare_fp64_m1},
-                                    {rhs_prepare_mixed_m0, rhs_prepare_mixed_m1},
-                                    {rhs_prepare_fp64_m0_prim, rhs_prepare_fp64_m1_prim},
-                                    {rhs_prepare_mixed_m0_prim, rhs_prepare_mixed_m1_prim}};
-const launch_fn k_launch[4][2] = {{rhs_launch_fp64_m0, rhs_launch_fp64_m1},
-                                  {rhs_launch_mixed_m0, rhs_launch_mixed_m1},
-                                  {rhs_launch_fp64_m0_prim, rhs_launch_fp64_m1_prim},
-                                  {rhs_launch_mixed_m0_prim, rhs_launch_mixed_m1_prim}};
+const prepare_fn k_prepare[4][RHS_MODES] = {
+    {rhs_prepare_fp64_m0, rhs_prepare_fp64_m1, rhs_prepare_fp64_m2},
+    {rhs_prepare_mixed_m0, rhs_prepare_mixed_m1, rhs_prepare_mixed_m2},
+    {rhs_prepare_fp64_m0_prim, rhs_prepare_fp64_m1_prim, rhs_prepare_fp64_m2_prim},
+    {rhs_prepare_mixed_m0_prim, rhs_prepare_mixed_m1_prim, rhs_prepare_mixed_m2_prim}};
+const launch_fn k_launch[4][RHS_MODES] = {
+    {rhs_launch_fp64_m0, rhs_launch_fp64_m1, rhs_launch_fp64_m2},
+    {rhs_launch_mixed_m0, rhs_launch_mixed_m1, rhs_launch_mixed_m2},
+    {rhs_launch_fp64_m0_prim, rhs_launch_fp64_m1_prim, rhs_launch_fp64_m2_prim},
+    {rhs_launch_mixed_m0_prim, rhs_launch_mixed_m1_prim, rhs_launch_mixed_m2_prim}};
 }  // namespace
 
 size_t rhs_smem_bytes(int nf, int form, int mode)
 {
     const int precision = form & 1;
-    return smem_plan(nf, precision == 0 ? 8 : 4, precision != 0, 8, mode == 0 ? 8 : 4).total;
+    return smem_plan(nf, precision == 0 ? 8 : 4, precision != 0, 8, mode == 1 ? 4 : 8).total;
 }
 
 cudaError_t rhs_prepare(int form, int mode, int nf, int *ctas_per_sm)
 {
-    if (form < 0 || form > 3 || mode < 0 || mode > 1)
+    if (form < 0 || form > 3 || mode < 0 || mode >= RHS_MODES)
         return cudaErrorInvalidValue;
     return k_prepare[form][mode](nf, ctas_per_sm);
 }
 
 cudaError_t rhs_launch(int form, int mode, int grid, cudaStream_t stream, const RhsArgs &args)
 {
-    if (form < 0 || form > 3 || mode < 0 || mode > 1)
+    if (form < 0 || form > 3 || mode < 0 || mode >= RHS_MODES)
         return cudaErrorInvalidValue;
     return k_launch[form][mode](grid, stream, args);
 }

@@ -1,4 +1,4 @@
-// rhs_fp64_m0.cu -- the FP64 RHS kernel, tile capacity 8x8, conserved-field reconstruction.
+// rhs_fp64_m0.cu -- the FP64 RHS kernel, tile capacity 8x8, 256 threads, conserved-field reconstruction.
 #include "rhs_instance.cuh"
 
-OCT_RHS_INSTANCE(fp64_m0, double, false, 8, 8, 1, false)
+OCT_RHS_INSTANCE(fp64_m0, double, false, 8, 8, 1, false, 256)

@@ -1,4 +1,4 @@
-// rhs_fp64_m0_prim.cu -- the FP64 RHS kernel, tile capacity 8x8, primitive reconstruction.
+// rhs_fp64_m0_prim.cu -- the FP64 RHS kernel, tile capacity 8x8, 256 threads, primitive reconstruction.
 #include "rhs_instance.cuh"
 
-OCT_RHS_INSTANCE(fp64_m0_prim, double, false, 8, 8, 1, true)
+OCT_RHS_INSTANCE(fp64_m0_prim, double, false, 8, 8, 1, true, 256)

@@ -1,13 +1,13 @@
 // rhs_instance.cuh -- host entry points of one RHS kernel instance.  Each
-// instance (FP64 or mixed form, tile capacity 8x8 or 8x4, conserved or
-// primitive reconstruction) is compiled in a translation unit of its own so
+// instance (FP64 or mixed form, launch shape -- 8x8 tiles with 256 or 512
+// threads, 8x4 tiles with 256 --, conserved or primitive reconstruction) is compiled in a translation unit of its own so
 // that the instances build in parallel; each unit uploads its own copy of the
 // line-group tables into its constant memory.
 #pragma once
 #include "rhs_kernel.cuh"
 #include "rhs_launch.h"
 
-#define OCT_RHS_INSTANCE(NAME, T, STAGED, TXM, TYM, MINB, PRIM)                                               \
+#define OCT_RHS_INSTANCE(NAME, T, STAGED, TXM, TYM, MINB, PRIM, NT)                                               \
     namespace octh {                                                                                          \
     cudaError_t rhs_prepare_##NAME(int nf, int *ctas_per_sm)                                                  \
     {                                                                                                         \
@@ -18,18 +18,18 @@
         if (t != cudaSuccess)                                                                                 \
             return t;                                                                                         \
         const size_t sm = smem_plan(nf, sizeof(T), STAGED, TXM, TYM).total;                                   \
-        cudaError_t e = cudaFuncSetAttribute(rhs_kernel<T, STAGED, TXM, TYM, MINB, PRIM>,                     \
+        cudaError_t e = cudaFuncSetAttribute(rhs_kernel<T, STAGED, TXM, TYM, MINB, PRIM, NT>,                     \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);           \
         if (e != cudaSuccess)                                                                                 \
             return e;                                                                                         \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm,                                     \
-                                                             rhs_kernel<T, STAGED, TXM, TYM, MINB, PRIM>,     \
-                                                             NTHREADS, sm);                                   \
+                                                             rhs_kernel<T, STAGED, TXM, TYM, MINB, PRIM, NT>,     \
+                                                             NT, sm);                                         \
     }                                                                                                         \
     cudaError_t rhs_launch_##NAME(int grid, cudaStream_t stream, const RhsArgs &args)                         \
     {                                                                                                         \
         const size_t sm = smem_plan(args.nf, sizeof(T), STAGED, TXM, TYM).total;                              \
-        rhs_kernel<T, STAGED, TXM, TYM, MINB, PRIM><<<grid, NTHREADS, sm, stream>>>(args);                    \
+        rhs_kernel<T, STAGED, TXM, TYM, MINB, PRIM, NT><<<grid, NT, sm, stream>>>(args);                          \
         return cudaGetLastError();                                                                            \
     }                                                                                                         \
     }

@@ -385,7 +385,7 @@ __device__ __forceinline__ void sfor(F &&f)
 // Phase A of line group G: 1-D PPM of every (line, field, cell), both ends
 // into the group buffer.  The line steps are compile-time constants; the
 // items are ordered line, field, cell.
-template <class T, bool STAGED, int G>
+template <class T, bool STAGED, int G, int NT>
 __device__ __forceinline__ void phase_a(T *temp, const float *raw, const double *Ub, long long FS, int B, int x0,
                                         int y0, int kz, bool inplane, int nf, int NC, int RWX, int plane,
                                         const int *lists, const int *nlist, const unsigned *magic, const int *so,
@@ -398,7 +398,7 @@ __device__ __forceinline__ void phase_a(T *temp, const float *raw, const double 
     const unsigned mg = magic[t];
     const int per = n * nf;
     const int *lst = lists + t * NC;
-    for (int q = tid; q < NL * per; q += NTHREADS) {
+    for (int q = tid; q < NL * per; q += NT) {
         sfor<NL>([&](auto Lc) {
             constexpr int L = decltype(Lc)::value;
             if (q >= L * per && q < (L + 1) * per) {
@@ -436,8 +436,9 @@ __device__ __forceinline__ void phase_a(T *temp, const float *raw, const double 
 // (rho, v, p, tau, X_i) and PPM reconstructs them; each point is turned back
 // into conserved fields (s = rho v, E = p/(gamma-1) + rho |v|^2/2,
 // rho_i = rho X_i) with its reconstructed v and p kept for the flux.
-template <class T, bool STAGED, int TXM, int TYM, int MINB, bool PRIM>
-__global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
+// NT: threads per CTA (256, or 512 for one CTA per SM over 8x8 tiles).
+template <class T, bool STAGED, int TXM, int TYM, int MINB, bool PRIM, int NT>
+__global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     // FP64: primitives once per point, shared through shared memory (FP64
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
     constexpr int FXS = (TXM + 1) * TYM;           // x faces of a full tile
     constexpr int FYS = TXM * (TYM + 1);           // y faces
     constexpr int XW = (FXS + 31) / 32 * 32, YW = (FYS + 31) / 32 * 32, ZW = (C64 + 31) / 32 * 32;
-    static_assert(XW + YW + ZW <= NTHREADS, "face threads exceed the block");
+    static_assert(XW + YW + ZW <= NT, "face threads exceed the block");
     T *temp = reinterpret_cast<T *>(smem + P.temp);    // [8 slots][nf][NC] point values of the group
     T *saved = reinterpret_cast<T *>(smem + P.saved);  // [9][nf][64] +z ends of the previous plane
     T *pr = reinterpret_cast<T *>(smem + P.pr);        // [8 slots][5][NC] vx, vy, vz, p, c of the group
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                 int slot = (kz + 3) % 5;
                 int rows = ty + 2 * NG, cols = tx + 2 * NG;
                 int n = nf * rows * cols;
-                for (int q = tid; q < n; q += NTHREADS) {
+                for (int q = tid; q < n; q += NT) {
                     int f = q / (rows * cols), r = q - f * (rows * cols);
                     int jj = r / cols, ii = r - jj * cols;
                     double v = __ldg(Ub + f * FS + (long long)(kz + NG) * B * B + (long long)(y0 + jj) * B + (x0 + ii));
@@ -516,7 +517,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
         nlist[1] = ncin + 2 * ty;
         nlist[2] = ncin + 2 * tx;
         nlist[3] = ncin + 2 * tx + 2 * ty;
-        for (int q = tid; q < 4 * NC; q += NTHREADS) {
+        for (int q = tid; q < 4 * NC; q += NT) {
             int t = q / NC, c = q % NC;
             if (c >= nlist[t])
                 continue;
@@ -572,7 +573,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                 switch (g) {
 #define OCT_PHASE_A(GG)                                                                                              \
     case GG:                                                                                                         \
-        phase_a<T, STAGED, GG>(temp, raw, Ub, FS, B, x0, y0, kz, inplane, nf, NC, RWX, RWY * RWX, lists, nlist,     \
+        phase_a<T, STAGED, GG, NT>(temp, raw, Ub, FS, B, x0, y0, kz, inplane, nf, NC, RWX, RWY * RWX, lists, nlist,     \
                                magic, so, tid);                                                                      \
         break;
                     OCT_PHASE_A(0)
@@ -594,7 +595,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                     const int m0 = per_in + (n0 - ncin), m1 = nl > 1 ? per_in + (n1 - ncin) : 0,
                               m2 = nl > 2 ? per_in + (n2 - ncin) : 0, m3 = nl > 3 ? per_in + (n3 - ncin) : 0;
                     const int tot = m0 + m1 + m2 + m3;
-                    for (int q = tid; q < tot; q += NTHREADS) {
+                    for (int q = tid; q < tot; q += NT) {
                         int l = 0, r = q, t = t0;
                         if (r >= m0) {
                             r -= m0;
@@ -817,7 +818,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
             // face is done) and the in-plane part of plane kz's, by the same
             // thread for each (field, cell), so dxy is read before it is
             // rewritten; then the next plane is staged ----
-            for (int q = tid; q < nf * ncin; q += NTHREADS) {
+            for (int q = tid; q < nf * ncin; q += NT) {
                 int f = q / ncin, c = q - f * ncin;
                 int i = c % tx, j = c / tx;
                 if (kz >= 1) {
@@ -841,7 +842,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                     // the subgrid's -z (below plane 0) or +z (above plane E-1) face
                     const T *zs = zacc + ((kz == 1 ? kz - 1 : kz) & 1) * nf * C64;
                     double *o = fb + (long long)(kz == 1 ? 4 : 5) * nf * E * E;
-                    for (int q = tid; q < nf * ncin; q += NTHREADS) {
+                    for (int q = tid; q < nf * ncin; q += NT) {
                         int f = q / ncin, c = q - f * ncin;
                         int i = c % tx, j = c / tx;
                         o[(long long)f * E * E + (y0 + j) * E + (x0 + i)] = Num<T>::to_d(zs[f * C64 + c]);
@@ -852,7 +853,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                     // x and y faces of plane kz on the subgrid's boundary
                     const long long EE = (long long)E * E;
                     if (x0 == 0 || x0 + tx == E)
-                        for (int q = tid; q < nf * ty; q += NTHREADS) {
+                        for (int q = tid; q < nf * ty; q += NT) {
                             int f = q / ty, j = q - f * ty;
                             const T *fx = faccx + f * FXS + j * (tx + 1);
                             const long long o = f * EE + (long long)kz * E + (y0 + j);
@@ -862,7 +863,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
                                 fb[nf * EE + o] = Num<T>::to_d(fx[tx]);
                         }
                     if (y0 == 0 || y0 + ty == E)
-                        for (int q = tid; q < nf * tx; q += NTHREADS) {
+                        for (int q = tid; q < nf * tx; q += NT) {
                             int f = q / tx, i = q - f * tx;
                             const T *fy = faccy + f * FYS;
                             const long long o = f * EE + (long long)kz * E + (x0 + i);
@@ -885,7 +886,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) rhs_kernel(RhsArgs A)
         __syncthreads();
         if (tid == 0) {
             double m = 0.0;
-            for (int w = 0; w < NTHREADS / 32; w++)
+            for (int w = 0; w < NT / 32; w++)
                 m = fmax(m, red[w]);
             A.amax_tile[it] = m;
         }

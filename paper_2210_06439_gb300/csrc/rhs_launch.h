@@ -1,7 +1,7 @@
 // rhs_launch.h -- host launchers of the RHS kernel instances.  Each instance
 // (FP64 or mixed, tile capacity 8x8 or 8x4, conserved or primitive
 // reconstruction) is compiled in a translation unit of its own
-// (rhs_<form>_<capacity>[_prim].cu) so the eight build in parallel.
+// (rhs_<form>_m<mode>[_prim].cu) so that they build in parallel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -9,9 +9,11 @@
 
 namespace octh {
 
-// form: precision (0 FP64, 1 mixed) + 2 for primitive reconstruction; mode:
-// 0 tile capacity 8x8 (one CTA per SM), 1 capacity 8x4 (two CTAs per SM for
-// FP64, three for the mixed form).
+// form: precision (0 FP64, 1 mixed) + 2 for primitive reconstruction; mode
+// (the launch shape): 0 tile capacity 8x8 with 256 threads (one CTA per SM),
+// 1 capacity 8x4 with 256 threads (two CTAs per SM for FP64, three for the
+// mixed form), 2 capacity 8x8 with 512 threads (one CTA per SM).
+constexpr int RHS_MODES = 3;
 size_t rhs_smem_bytes(int nf, int form, int mode);
 bool build_group_tables(GroupTab *groups);
 cudaError_t rhs_prepare(int form, int mode, int nf, int *ctas_per_sm);

@@ -1,0 +1,4 @@
+// rhs_mixed_m2_prim.cu -- the mixed RHS kernel, tile capacity 8x8, 512 threads, primitive reconstruction.
+#include "rhs_instance.cuh"
+
+OCT_RHS_INSTANCE(mixed_m2_prim, float, true, 8, 8, 1, true, 512)
