@@ -205,6 +205,8 @@ def _noisy_gas_law(seed, counter, gamma=GAMMA, n_species=5):
     p = np.maximum(p0 * (1.0 + 0.1 * normal(seed, 2, counter)), 1e-3 * p0)
     cs = np.sqrt(gamma * p / rho)
     v = [0.3 * cs * normal(seed, 3 + i, counter) for i in range(3)]
+    if n_species == 0:
+        return conserved(rho, v[0], v[1], v[2], p, [], gamma)
     w = np.stack([uniform(seed, 20 + i, counter) for i in range(n_species)])
     w = w / np.sum(w, axis=0)
     return conserved(rho, v[0], v[1], v[2], p, [w[i] * rho for i in range(n_species)], gamma)

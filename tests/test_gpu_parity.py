@@ -227,3 +227,10 @@ def test_dt_cap_applies_to_replayed_graphs():
     dt_now = H.max_dt(U, stream=st)
     assert H.rk_step(U, stream=st) == dt_now
     assert H.error_flags() == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n_species", [0, 1, 3])
+def test_species_counts(n_species, precision):
+    """Field counts other than 11: no species (6 fields), one and three."""
+    _check_rhs(inputs.periodic_box(nsub=2, n_species=n_species), precision)
