@@ -45,6 +45,9 @@
  *       the mean of the 8 finer cells (restriction);
  *   R15 flux correction at coarse-fine faces: the coarse flux through such
  *       a face is replaced by the mean of the 4 fine fluxes on it;
+ *   R17 (optional) limited linear prolongation instead of injection: the
+ *       coarse value plus a quarter of each axis's minmod slope, signed by
+ *       the fine cell's side;
  *   R16 (optional, recon = 1) primitive reconstruction: PPM acts on
  *       w = (rho, v, p, tau, X_i = rho_i / rho) of every cell, and each point
  *       is turned back into conserved fields (s = rho v,
@@ -747,7 +750,10 @@ int oco_amr_reflux(int n_sub, int E, const double *dx, int nf, const int32_t *le
 typedef struct {
     const int32_t *lev, *org;
     int n0, periodic;
+    int order; /* prolongation order (reading R17): 0 injection, 1 limited linear */
 } oco_amr;
+int oco_amr_ghost_fill_order(int n_sub, int E, const int64_t *off, int nf, const int32_t *lev, const int32_t *org,
+                             int n0, int periodic, int order, double *U);
 
 static int rk3_step_impl(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf, double gamma,
                          double eps1, double eps2, double rho_floor, double cfl, double dt_cap, int bc,
@@ -788,7 +794,18 @@ int oco_rk3_step_amr(int n_sub, const int32_t *edge, const int64_t *off, const d
                      const int32_t *org, int n0, int periodic, double *U, int64_t total_len, double *dt_out,
                      int64_t *floors_out, int nthreads)
 {
-    oco_amr a = {lev, org, n0, periodic};
+    oco_amr a = {lev, org, n0, periodic, 0};
+    return rk3_step_impl(n_sub, edge, off, dx, nf, gamma, eps1, eps2, rho_floor, cfl, dt_cap, 3, NULL, &a, 0, U,
+                         total_len, dt_out, floors_out, nthreads);
+}
+
+/* oco_rk3_step_amr with the prolongation order of the ghost fill (R17). */
+int oco_rk3_step_amr_order(int n_sub, const int32_t *edge, const int64_t *off, const double *dx, int nf,
+                           double gamma, double eps1, double eps2, double rho_floor, double cfl, double dt_cap,
+                           const int32_t *lev, const int32_t *org, int n0, int periodic, int order, double *U,
+                           int64_t total_len, double *dt_out, int64_t *floors_out, int nthreads)
+{
+    oco_amr a = {lev, org, n0, periodic, order};
     return rk3_step_impl(n_sub, edge, off, dx, nf, gamma, eps1, eps2, rho_floor, cfl, dt_cap, 3, NULL, &a, 0, U,
                          total_len, dt_out, floors_out, nthreads);
 }
@@ -835,7 +852,8 @@ static int rk3_step_impl(int n_sub, const int32_t *edge, const int64_t *off, con
         oco_rk_combine(stage, n_sub, edge, off, nf, dt, U0, L, U);
         fired += oco_floors(n_sub, edge, off, nf, gamma, rho_floor, eps2, U);
         if (bc == 3) {
-            if (oco_amr_ghost_fill(n_sub, edge[0], off, nf, amr->lev, amr->org, amr->n0, amr->periodic, U) != 0) {
+            if (oco_amr_ghost_fill_order(n_sub, edge[0], off, nf, amr->lev, amr->org, amr->n0, amr->periodic,
+                                         amr->order, U) != 0) {
                 bad = -2;
                 break;
             }
@@ -1038,5 +1056,142 @@ int oco_amr_reflux(int n_sub, int E, const double *dx, int nf, const int32_t *le
                     }
         }
     }
+    return err ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ghost fill across levels with limited linear prolongation (reading R17)   */
+/* ------------------------------------------------------------------------ */
+
+/* minmod of the two one-sided differences a = u(+1) - u(0), b = u(0) - u(-1):
+ * the smaller in magnitude when both have the same strict sign, else 0. */
+static double minmod2(double a, double b)
+{
+    if (!(a * b > 0.0))
+        return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+/* As oco_amr_ghost_fill, with the prolongation order chosen by order:
+ * 0 = injection (the fine ghost takes the covering coarse cell's value);
+ * 1 = limited linear: the coarse value plus, per axis, a quarter of the
+ *     minmod slope of the coarse cell and its two neighbours along that axis
+ *     in the coarse subgrid's ghosted block, with the sign of the fine cell's
+ *     offset from the coarse centre (+ for the upper child).  Sum order:
+ *     t = s_x d_x; t = t + s_y d_y; t = t + s_z d_z; value = u + t / 4.
+ *     A neighbour that is itself a ghost cell filled by prolongation is not
+ *     used (zero slope on that axis), so the result does not depend on the
+ *     order in which ghost cells are filled.
+ * Copies and restrictions are done first, prolongations second (they read
+ * the coarse blocks' ghost cells).  The 8 children of a coarse cell average
+ * to its value.  Returns 0, or -2 when some ghost cell has no source. */
+int oco_amr_ghost_fill_order(int n_sub, int E, const int64_t *off, int nf, const int32_t *lev, const int32_t *org,
+                             int n0, int periodic, int order, double *U)
+{
+    if (!valid_edge(E) || order < 0 || order > 1)
+        return -1;
+    int B = E + 2 * NG;
+    int64_t fs = (int64_t)B * B * B;
+    /* kind of every cell of every block: 0 interior, 1 copy, 2 restriction,
+     * 3 prolongation; and, for prolongations, the coarse source */
+    uint8_t *kind = (uint8_t *)calloc((size_t)n_sub * fs, 1);
+    int32_t *src_t = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_sub * fs);
+    int64_t *src_c = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_sub * fs);
+    uint8_t *par = (uint8_t *)calloc((size_t)n_sub * fs, 1);
+    int err = 0;
+    for (int pass = 1; pass <= 2; pass++)
+        for (int s = 0; s < n_sub; s++) {
+            int l = lev[s];
+            int64_t nl = (int64_t)n0 << l;
+            for (int z = -NG; z < E + NG; z++)
+                for (int y = -NG; y < E + NG; y++)
+                    for (int x = -NG; x < E + NG; x++) {
+                        if (x >= 0 && x < E && y >= 0 && y < E && z >= 0 && z < E)
+                            continue;
+                        int64_t dl = cidx(B, x + NG, y + NG, z + NG);
+                        int64_t dst = off[s] + dl;
+                        if (pass == 2) {
+                            if (kind[(int64_t)s * fs + dl] != 3)
+                                continue;
+                            /* limited linear prolongation from the coarse cell */
+                            int t = src_t[(int64_t)s * fs + dl];
+                            int64_t cl = src_c[(int64_t)s * fs + dl];
+                            int p = par[(int64_t)s * fs + dl];
+                            int64_t step[3] = {1, B, (int64_t)B * B};
+                            for (int f = 0; f < nf; f++) {
+                                const double *u = U + off[t] + f * fs;
+                                double acc = 0.0;
+                                for (int a = 0; a < 3; a++) {
+                                    int64_t up = cl + step[a], dn = cl - step[a];
+                                    double d = 0.0;
+                                    if (kind[(int64_t)t * fs + up] != 3 && kind[(int64_t)t * fs + dn] != 3)
+                                        d = minmod2(u[up] - u[cl], u[cl] - u[dn]);
+                                    double sd = (p >> a) & 1 ? d : -d;
+                                    acc = a == 0 ? sd : acc + sd;
+                                }
+                                U[dst + f * fs] = u[cl] + acc / 4.0;
+                            }
+                            continue;
+                        }
+                        int64_t g[3] = {org[3 * s] + x, org[3 * s + 1] + y, org[3 * s + 2] + z};
+                        for (int a = 0; a < 3; a++) {
+                            if (periodic)
+                                g[a] = ((g[a] % nl) + nl) % nl;
+                            else
+                                g[a] = g[a] < 0 ? 0 : (g[a] >= nl ? nl - 1 : g[a]);
+                        }
+                        int t = find_cover(n_sub, E, lev, org, l, g);
+                        if (t >= 0) {
+                            int64_t src = off[t] + cidx(B, (int)(g[0] - org[3 * t]) + NG, (int)(g[1] - org[3 * t + 1]) + NG,
+                                                        (int)(g[2] - org[3 * t + 2]) + NG);
+                            for (int f = 0; f < nf; f++)
+                                U[dst + f * fs] = U[src + f * fs];
+                            kind[(int64_t)s * fs + dl] = 1;
+                            continue;
+                        }
+                        if (l > 0) {
+                            int64_t gc[3] = {g[0] >> 1, g[1] >> 1, g[2] >> 1};
+                            t = find_cover(n_sub, E, lev, org, l - 1, gc);
+                            if (t >= 0) {
+                                int64_t cl = cidx(B, (int)(gc[0] - org[3 * t]) + NG, (int)(gc[1] - org[3 * t + 1]) + NG,
+                                                  (int)(gc[2] - org[3 * t + 2]) + NG);
+                                if (order == 0) {
+                                    for (int f = 0; f < nf; f++)
+                                        U[dst + f * fs] = U[off[t] + cl + f * fs];
+                                    kind[(int64_t)s * fs + dl] = 1;
+                                } else {
+                                    kind[(int64_t)s * fs + dl] = 3;
+                                    src_t[(int64_t)s * fs + dl] = t;
+                                    src_c[(int64_t)s * fs + dl] = cl;
+                                    par[(int64_t)s * fs + dl] =
+                                        (uint8_t)((g[0] & 1) | ((g[1] & 1) << 1) | ((g[2] & 1) << 2));
+                                }
+                                continue;
+                            }
+                        }
+                        int64_t gf[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
+                        t = find_cover(n_sub, E, lev, org, l + 1, gf);
+                        if (t < 0) {
+                            err = 1;
+                            continue;
+                        }
+                        for (int f = 0; f < nf; f++) {
+                            double sum = 0.0;
+                            for (int dz = 0; dz < 2; dz++)
+                                for (int dy = 0; dy < 2; dy++)
+                                    for (int dx = 0; dx < 2; dx++)
+                                        sum += U[off[t] + f * fs +
+                                                 cidx(B, (int)(gf[0] + dx - org[3 * t]) + NG,
+                                                      (int)(gf[1] + dy - org[3 * t + 1]) + NG,
+                                                      (int)(gf[2] + dz - org[3 * t + 2]) + NG)];
+                            U[dst + f * fs] = sum / 8.0;
+                        }
+                        kind[(int64_t)s * fs + dl] = 2;
+                    }
+        }
+    free(kind);
+    free(src_t);
+    free(src_c);
+    free(par);
     return err ? -2 : 0;
 }

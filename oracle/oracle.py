@@ -91,6 +91,11 @@ def _declare(L):
     L.oco_rk3_step.restype = _I
     L.oco_amr_ghost_fill.argtypes = [_I, _I, _P, _I, _P, _P, _I, _I, _P]
     L.oco_amr_ghost_fill.restype = _I
+    L.oco_amr_ghost_fill_order.argtypes = [_I, _I, _P, _I, _P, _P, _I, _I, _I, _P]
+    L.oco_amr_ghost_fill_order.restype = _I
+    L.oco_rk3_step_amr_order.argtypes = [_I, _P, _P, _P, _I, _D, _D, _D, _D, _D, _D, _P, _P, _I, _I, _I, _P, _I64, _P,
+                                         _P, _I]
+    L.oco_rk3_step_amr_order.restype = _I
     L.oco_rk3_step_amr.argtypes = [_I, _P, _P, _P, _I, _D, _D, _D, _D, _D, _D, _P, _P, _I, _I, _P, _I64, _P, _P, _I]
     L.oco_rk3_step_amr.restype = _I
 
@@ -250,25 +255,31 @@ def rk3_step(edge, off, dx, nf, U, bc, nbr=None, gamma=5.0 / 3.0, eps1=1e-3, eps
     return float(dt[0]), int(fired[0]), int(st)
 
 
-def amr_ghost_fill(E, off, nf, level, origin, n0, periodic, U):
+def amr_ghost_fill(E, off, nf, level, origin, n0, periodic, U, order=0):
     """In-place ghost fill across refinement levels (same level, coarser by
-    injection, finer by 8-cell mean); origin is [n, 3] in cells of each level."""
+    injection (order 0) or limited linear prolongation (order 1), finer by
+    8-cell mean); origin is [n, 3] in cells of each level."""
     off, lev, org = _i64(off), _i32(level), _i32(origin).reshape(-1)
     assert U.dtype == np.float64 and U.flags.c_contiguous
-    r = lib().oco_amr_ghost_fill(off.shape[0], int(E), _p(off), int(nf), _p(lev), _p(org), int(n0), int(periodic),
-                                 _p(U))
+    if order == 0:
+        r = lib().oco_amr_ghost_fill(off.shape[0], int(E), _p(off), int(nf), _p(lev), _p(org), int(n0),
+                                     int(periodic), _p(U))
+    else:
+        r = lib().oco_amr_ghost_fill_order(off.shape[0], int(E), _p(off), int(nf), _p(lev), _p(org), int(n0),
+                                           int(periodic), int(order), _p(U))
     if r != 0:
         raise ValueError(f"oracle amr_ghost_fill failed ({r})")
 
 
 def rk3_step_amr(edge, off, dx, nf, U, level, origin, n0, periodic, gamma=5.0 / 3.0, eps1=1e-3, eps2=0.1,
-                 rho_floor=1e-12, cfl=0.4, dt_cap=0.0, nthreads=0):
-    """One SSP-RK3 step in place with the ghost fill across levels."""
+                 rho_floor=1e-12, cfl=0.4, dt_cap=0.0, nthreads=0, order=0):
+    """One SSP-RK3 step in place with the ghost fill across levels
+    (prolongation order as in amr_ghost_fill)."""
     edge, off, dx = _i32(edge), _i64(off), _f64(dx)
     lev, org = _i32(level), _i32(origin).reshape(-1)
     assert U.dtype == np.float64 and U.flags.c_contiguous
     dt, fired = np.zeros(1), np.zeros(1, np.int64)
-    st = lib().oco_rk3_step_amr(edge.shape[0], _p(edge), _p(off), _p(dx), int(nf), gamma, eps1, eps2, rho_floor,
-                                cfl, float(dt_cap), _p(lev), _p(org), int(n0), int(periodic), _p(U), U.size, _p(dt),
-                                _p(fired), int(nthreads))
+    st = lib().oco_rk3_step_amr_order(edge.shape[0], _p(edge), _p(off), _p(dx), int(nf), gamma, eps1, eps2,
+                                      rho_floor, cfl, float(dt_cap), _p(lev), _p(org), int(n0), int(periodic),
+                                      int(order), _p(U), U.size, _p(dt), _p(fired), int(nthreads))
     return float(dt[0]), int(fired[0]), int(st)

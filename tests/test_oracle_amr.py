@@ -242,3 +242,124 @@ def test_amr_rk3_step_conserves():
     t1, _ = _volume_totals(p, after)
     for f in range(5):
         assert abs(t1[f] - t0[f]) <= 1e-14 * sc[f], (f, (t1[f] - t0[f]) / sc[f])
+
+
+# ---------------------------------------------------------------------------
+# Limited linear prolongation (order 1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_order0_of_the_general_fill_is_the_injection_fill(periodic):
+    p = inputs.amr_box(periodic=periodic)
+    m = p.meta
+    a, b = p.U.copy(), p.U.copy()
+    oracle.amr_ghost_fill(8, p.off, p.nf, m["level"], m["origin"], m["n0"], periodic, a)
+    lib = oracle.lib()
+    lev, org = np.ascontiguousarray(m["level"], np.int32), np.ascontiguousarray(m["origin"], np.int32).reshape(-1)
+    off = np.ascontiguousarray(p.off, np.int64)
+    r = lib.oco_amr_ghost_fill_order(p.n_sub, 8, off.ctypes.data, p.nf, lev.ctypes.data, org.ctypes.data,
+                                     int(m["n0"]), int(periodic), 0, b.ctypes.data)
+    assert r == 0
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_linear_prolongation_reproduces_a_linear_field(periodic):
+    """With slopes from a linear field (equal one-sided differences, so the
+    minmod keeps them) every ghost cell -- copy, restriction or prolongation --
+    gets the field's value at its own centre, exactly (dyadic values)."""
+    p = inputs.amr_box(n_coarse=4, E=8, periodic=periodic)
+    E, n0 = 8, p.meta["n0"]
+    lev, org = p.meta["level"], p.meta["origin"]
+    coef = _coefs(p.nf)
+    _linear_fill(p, coef)
+    oracle.amr_ghost_fill(E, p.off, p.nf, lev, org, n0, periodic, p.U, order=1)
+    B = E + 2 * NG
+    r = np.arange(-NG, E + NG)
+    gz, gy, gx = np.meshgrid(r, r, r, indexing="ij")
+    ghost = ~((gx >= 0) & (gx < E) & (gy >= 0) & (gy < E) & (gz >= 0) & (gz < E))
+    for s in range(p.n_sub):
+        l = int(lev[s])
+        nl = n0 << l
+        g = [org[s, 0] + gx, org[s, 1] + gy, org[s, 2] + gz]
+        g = [np.mod(v, nl) if periodic else np.clip(v, 0, nl - 1) for v in g]
+        cen = [(v + 0.5) / (2 ** l) for v in g]
+        blk = p.U[p.off[s]: p.off[s] + p.nf * B ** 3].reshape(p.nf, B, B, B)
+        for f in range(p.nf):
+            a, b, c, d = coef[f]
+            want = a + b * cen[0] + c * cen[1] + d * cen[2]
+            np.testing.assert_array_equal(blk[f][ghost], want[ghost])
+
+
+def test_linear_prolongation_keeps_means_and_bounds():
+    """On the noisy field: the prolonged children of a coarse cell lie within
+    the range of that coarse cell and its six face neighbours (the minmod
+    limiter adds no extremum), and where all 8 children of a coarse cell are
+    ghost cells of one fine subgrid their mean is the coarse value."""
+    p = inputs.amr_box()
+    E, B, n0 = 8, 14, p.meta["n0"]
+    lev, org = p.meta["level"], p.meta["origin"]
+    oracle.amr_ghost_fill(E, p.off, p.nf, lev, org, n0, True, p.U, order=1)
+    q = inputs.amr_box()  # the coarse values around, from the copies and restrictions of order 0
+    oracle.amr_ghost_fill(E, q.off, q.nf, lev, org, n0, True, q.U, order=0)
+    coarse = {}
+    for s in range(p.n_sub):
+        if lev[s] == 0:
+            coarse[tuple(org[s] // E)] = s
+    n_checked = n_means = 0
+    for s in range(p.n_sub):
+        if lev[s] != 1:
+            continue
+        blk = p.U[p.off[s]: p.off[s] + p.nf * B ** 3].reshape(p.nf, B, B, B)
+        groups = {}
+        for z in range(-NG, E + NG):
+            for y in range(-NG, E + NG):
+                for x in range(-NG, E + NG):
+                    if 0 <= x < E and 0 <= y < E and 0 <= z < E:
+                        continue
+                    g = [(org[s, 0] + x) % (2 * n0), (org[s, 1] + y) % (2 * n0), (org[s, 2] + z) % (2 * n0)]
+                    gc = [v >> 1 for v in g]
+                    key = tuple(v // E for v in gc)
+                    if key not in coarse:
+                        continue  # a same-level copy
+                    t = coarse[key]
+                    cb = q.U[q.off[t]: q.off[t] + q.nf * B ** 3].reshape(q.nf, B, B, B)
+                    lc = [gc[a] - org[t, a] + NG for a in range(3)]
+                    nb = [cb[:, lc[2], lc[1], lc[0]]]
+                    for a in range(3):
+                        for st in (-1, 1):
+                            ll = list(lc)
+                            ll[a] += st
+                            nb.append(cb[:, ll[2], ll[1], ll[0]])
+                    nb = np.stack(nb)
+                    v = blk[:, z + NG, y + NG, x + NG]
+                    lo, hi = nb.min(axis=0), nb.max(axis=0)
+                    tol = 1e-15 * np.maximum(np.abs(lo), np.abs(hi))
+                    assert np.all(v >= lo - tol) and np.all(v <= hi + tol)
+                    n_checked += 1
+                    groups.setdefault(tuple(gc), []).append(v)
+        for gc, vs in groups.items():
+            if len(vs) == 8:
+                t = coarse[tuple(v // E for v in gc)]
+                cb = q.U[q.off[t]: q.off[t] + q.nf * B ** 3].reshape(q.nf, B, B, B)
+                uc = cb[:, gc[2] - org[t, 2] + NG, gc[1] - org[t, 1] + NG, gc[0] - org[t, 0] + NG]
+                np.testing.assert_allclose(np.mean(vs, axis=0), uc, rtol=1e-14,
+                                           atol=1e-14 * float(np.max(np.abs(vs))))
+                n_means += 1
+    assert n_checked > 1000 and n_means > 10
+
+
+def test_amr_rk3_step_with_linear_prolongation_conserves():
+    p = inputs.amr_box()
+    m = p.meta
+    oracle.amr_ghost_fill(8, p.off, p.nf, m["level"], m["origin"], m["n0"], m["periodic"], p.U, order=1)
+    from tests.helpers import interior_layout
+    before = interior_layout(p.U, p)
+    dt, fired, st = oracle.rk3_step_amr(p.edge, p.off, p.dx, p.nf, p.U, m["level"], m["origin"], m["n0"],
+                                        m["periodic"], gamma=p.gamma, order=1)
+    assert st == 0 and fired == 0 and dt > 0
+    after = interior_layout(p.U, p)
+    t0, sc = _volume_totals(p, before)
+    t1, _ = _volume_totals(p, after)
+    for f in range(5):
+        assert abs(t1[f] - t0[f]) <= 1e-14 * sc[f], (f, (t1[f] - t0[f]) / sc[f])
