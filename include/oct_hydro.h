@@ -137,6 +137,17 @@ oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, const int64
 oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, const int32_t *origin, int root_cells,
                              int periodic);
 
+/* Prolongation order of the ghost fill across levels (the order of the fine
+ * ghost cells under a coarse cell; the paper does not state it): 0 (the
+ * default) injection -- the coarse value; 1 limited linear -- the coarse value
+ * plus, per axis, a quarter of the minmod slope of the coarse cell and its
+ * two neighbours along that axis (neighbours that are themselves prolonged
+ * ghosts give no slope), signed + for the upper half: t = s_x d_x + s_y d_y
+ * + s_z d_z in that order, u + t/4.  The 8 children of a coarse cell average
+ * to its value and no new extremum appears.  Rebuilds the ghost plan when
+ * levels are set.  OCT_E_ARG for another order. */
+oct_status oct_hydro_set_prolongation(oct_hydro_t h, int order);
+
 /* Which variables PPM reconstructs (Sec. II "Solvers": the reconstruct
  * kernel yields point values of the evolved variables at 26 points per cell;
  * which variables it interpolates is not stated).  OCT_RECON_CONSERVED (the

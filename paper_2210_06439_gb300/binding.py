@@ -31,6 +31,7 @@ SIGNATURES = {
     "oct_hydro_set_layout": (_I, [_P, _P, _P, _P, _P, _P, _I]),
     "oct_hydro_set_amr": (_I, [_P, _P, _P, _I, _I]),
     "oct_hydro_set_reconstruction": (_I, [_P, _I]),
+    "oct_hydro_set_prolongation": (_I, [_P, _I]),
     "oct_hydro_set_params": (_I, [_P, _I, _D, _D, _D, _D]),
     "oct_hydro_set_dt_cap": (_I, [_P, _D]),
     "oct_hydro_state_len": (_I64, [_P]),
@@ -161,6 +162,9 @@ class Hydro:
         self._amr = [np.ascontiguousarray(level, np.int32), np.ascontiguousarray(origin, np.int32).reshape(-1)]
         check(self.L.oct_hydro_set_amr(self.h, self._amr[0].ctypes.data, self._amr[1].ctypes.data, int(root_cells),
                                        int(bool(periodic))))
+
+    def set_prolongation(self, order):
+        check(self.L.oct_hydro_set_prolongation(self.h, int(order)))
 
     def set_reconstruction(self, variables):
         check(self.L.oct_hydro_set_reconstruction(self.h, int(variables)))

@@ -96,6 +96,10 @@ struct oct_hydro {
            *d_Lhost = nullptr;
     unsigned *d_flags = nullptr;
     int2 *d_amr_plan = nullptr;  // ghost-cell sources across levels (OCT_BC_AMR)
+    std::vector<int32_t> amr_level, amr_origin;  // the levels as last set, for a rebuild
+    int amr_root = 0, amr_periodic = 0;
+    int prolong_order = 0;  // 0 injection, 1 limited linear
+    bool has_prolong = false;  // the plan holds limited linear prolongations
     double *d_faces = nullptr;     // boundary face fluxes of the subgrids next to a level change
     int *d_face_slot = nullptr;    // per subgrid: its slot in d_faces, or -1
     RefluxCorr *d_corr = nullptr;  // flux corrections at coarse-fine faces, grouped by coarse cell
@@ -481,7 +485,14 @@ extern "C" oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, con
             const long long cc[3] = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
             t = cover(l - 1, cc);
             if (t >= 0) {
-                plan[(size_t)s * G + q] = make_int2(t, (int)local(t, cc));
+                if (h->prolong_order == 0) {
+                    plan[(size_t)s * G + q] = make_int2(t, (int)local(t, cc));  // injection: a copy
+                } else {
+                    // limited linear: bit 30; which half of the coarse cell per axis in
+                    // bits 16..18 of y (the usable-slope mask follows below)
+                    const int par = (int)((c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2));
+                    plan[(size_t)s * G + q] = make_int2((int)(t | 0x40000000u), (int)local(t, cc) | (par << 16));
+                }
                 continue;
             }
             const long long cf[3] = {2 * c[0], 2 * c[1], 2 * c[2]};
@@ -489,6 +500,45 @@ extern "C" oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, con
             if (t < 0)
                 return fail(OCT_E_ARG, "ghost cell %d of subgrid %d has no source (levels not properly nested)", q, s);
             plan[(size_t)s * G + q] = make_int2((int)(t | 0x80000000u), (int)local(t, cf));
+        }
+    }
+    // limited linear prolongation: a slope axis is usable when both coarse
+    // neighbours are interior cells or ghosts filled by copy or restriction
+    bool has_prolong = false;
+    if (h->prolong_order == 1) {
+        const long long B3 = (long long)B * B * B;
+        std::vector<unsigned char> kind((size_t)n * B3, 0);  // 0 interior, 1 copy, 2 restriction, 3 prolongation
+        for (int q = 0; q < G; q++) {
+            int g[3];
+            if (q < 2 * nzs) {
+                const int r = q % nzs, side = q / nzs;
+                g[0] = r % B - NG, g[1] = (r / B) % B - NG, g[2] = r / (B * B) + (side ? E : -NG);
+            } else if (q < 2 * nzs + 2 * nys) {
+                const int r0 = q - 2 * nzs, r = r0 % nys, side = r0 / nys;
+                g[0] = r % B - NG, g[1] = (r / B) % NG + (side ? E : -NG), g[2] = r / (B * NG);
+            } else {
+                const int r0 = q - 2 * nzs - 2 * nys, r = r0 % nxs, side = r0 / nxs;
+                g[0] = r % NG + (side ? E : -NG), g[1] = (r / NG) % E, g[2] = r / (NG * E);
+            }
+            const long long gl = ((long long)(g[2] + NG) * B + (g[1] + NG)) * B + (g[0] + NG);
+            for (int s = 0; s < n; s++) {
+                const int2 e = plan[(size_t)s * G + q];
+                kind[(size_t)s * B3 + gl] = (e.x & 0x40000000) ? 3 : (e.x < 0 ? 2 : 1);
+            }
+        }
+        const long long step[3] = {1, B, (long long)B * B};
+        for (size_t i = 0; i < plan.size(); i++) {
+            int2 &e = plan[i];
+            if (!(e.x & 0x40000000) || e.x < 0)
+                continue;
+            has_prolong = true;
+            const int t = e.x & 0x3FFFFFFF;
+            const long long cl = e.y & 0xFFFF;
+            int mask = 0;
+            for (int a = 0; a < 3; a++)
+                if (kind[(size_t)t * B3 + cl + step[a]] != 3 && kind[(size_t)t * B3 + cl - step[a]] != 3)
+                    mask |= 1 << a;
+            e.y |= mask << 19;
         }
     }
     // flux corrections: every face between a cell and a finer region
@@ -577,7 +627,33 @@ extern "C" oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, con
         h->n_corr_cells = (int)first.size() - 1;
     }
     h->bc = OCT_BC_AMR;
+    h->has_prolong = has_prolong;
+    h->amr_level.assign(level, level + n);
+    h->amr_origin.assign(origin, origin + 3 * (size_t)n);
+    h->amr_root = root_cells;
+    h->amr_periodic = periodic;
     drop_graphs(h);
+    return OCT_OK;
+}
+
+extern "C" oct_status oct_hydro_set_prolongation(oct_hydro_t h, int order)
+{
+    DeviceGuard device_guard(h);
+    if (!h)
+        return fail(OCT_E_ARG, "handle is NULL");
+    if (order != 0 && order != 1)
+        return fail(OCT_E_ARG, "prolongation order must be 0 (injection) or 1 (limited linear) (got %d)", order);
+    const int prev = h->prolong_order;
+    h->prolong_order = order;
+    if (h->bc == OCT_BC_AMR && order != prev) {
+        // rebuild the ghost plan with the new order from the levels as last set
+        const std::vector<int32_t> lev = h->amr_level, org = h->amr_origin;
+        const oct_status st = oct_hydro_set_amr(h, lev.data(), org.data(), h->amr_root, h->amr_periodic);
+        if (st != OCT_OK) {
+            h->prolong_order = prev;
+            return st;
+        }
+    }
     return OCT_OK;
 }
 
@@ -760,8 +836,12 @@ static oct_status launch_ghosts(oct_hydro *h, double *U, cudaStream_t s)
     if (h->bc == OCT_BC_GIVEN)
         return OCT_OK;
     if (h->bc == OCT_BC_AMR) {
-        amr_ghost_kernel<<<h->n_sub, 256, 0, s>>>(U, h->edge[0], h->d_off, h->nf, h->d_amr_plan, h->d_flags);
+        amr_ghost_kernel<<<h->n_sub, 256, 0, s>>>(U, h->edge[0], h->d_off, h->nf, h->d_amr_plan, 0);
         CUDA_TRY(cudaGetLastError());
+        if (h->has_prolong) {  // prolongations read the coarse blocks' ghosts of the first pass
+            amr_ghost_kernel<<<h->n_sub, 256, 0, s>>>(U, h->edge[0], h->d_off, h->nf, h->d_amr_plan, 1);
+            CUDA_TRY(cudaGetLastError());
+        }
         return OCT_OK;
     }
     ghost_fill_kernel<<<h->n_sub, 256, 0, s>>>(U, h->edge[0], h->d_off, h->nf, h->d_nbr, h->d_flags);

@@ -249,10 +249,16 @@ __global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf
 
 // Ghost fill across refinement levels from a host-built plan: entry q of
 // subgrid s (ghost cells enumerated as in ghost_fill_kernel) holds the source
-// subgrid (bit 31 set: the mean of the 2x2x2 cells starting there,
-// otherwise a copy) and the source cell's index in its ghosted block.
-// Interiors are only read; the 8 cells of a mean are summed in z, y, x order.
-__global__ void amr_ghost_kernel(double *U, int E, const long long *off, int nf, const int2 *plan, unsigned *flags)
+// subgrid in x -- bit 31 set: the mean of the 2x2x2 cells starting at the
+// source index; bit 30 set: limited linear prolongation from that coarse
+// cell; neither: a copy -- and in y the source cell's index in its ghosted
+// block (bits 0..15), for a prolongation also the upper-half flags of the
+// fine cell per axis (bits 16..18) and the usable-slope axes (bits 19..21).
+// Pass 0 does the copies and means (they read interiors only), pass 1 the
+// prolongations (they also read coarse ghosts of pass 0).  The 8 cells of a
+// mean are summed in z, y, x order; a prolongation is u + t/4 with
+// t = s_x d_x + s_y d_y + s_z d_z summed in that order, d the minmod slope.
+__global__ void amr_ghost_kernel(double *U, int E, const long long *off, int nf, const int2 *plan, int pass)
 {
     const int s = blockIdx.x;
     const int B = E + 2 * NG;
@@ -261,6 +267,10 @@ __global__ void amr_ghost_kernel(double *U, int E, const long long *off, int nf,
     const int total = 2 * nzs + 2 * nys + 2 * nxs;
     const int2 *pl = plan + (long long)s * total;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int2 e = pl[q];
+        const bool prolong = (e.x & 0x40000000) && e.x >= 0;
+        if (prolong != (pass == 1))
+            continue;
         int g[3];
         if (q < 2 * nzs) {
             const int r = q % nzs, side = q / nzs;
@@ -279,11 +289,32 @@ __global__ void amr_ghost_kernel(double *U, int E, const long long *off, int nf,
             g[2] = r / (NG * E);
         }
         const long long di = off[s] + ((long long)(g[2] + NG) * B + (g[1] + NG)) * B + (g[0] + NG);
-        const int2 e = pl[q];
-        const int t = e.x & 0x7FFFFFFF;
-        const long long si = off[t] + e.y;
+        const int t = e.x & 0x3FFFFFFF;
         double v[MAXNF];
-        if (e.x < 0) {
+        if (prolong) {
+            const long long si = off[t] + (e.y & 0xFFFF);
+            const int par = (e.y >> 16) & 7, mask = (e.y >> 19) & 7;
+            const long long step[3] = {1, B, (long long)B * B};
+#pragma unroll
+            for (int f = 0; f < MAXNF; f++)
+                if (f < nf) {
+                    const double *c = U + si + f * FS;
+                    const double u = c[0];
+                    double acc = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        double d = 0.0;
+                        if ((mask >> a) & 1) {
+                            const double up = __dsub_rn(c[step[a]], u), dn = __dsub_rn(u, c[-step[a]]);
+                            d = __dmul_rn(up, dn) > 0.0 ? (fabs(up) < fabs(dn) ? up : dn) : 0.0;
+                        }
+                        const double sd = ((par >> a) & 1) ? d : -d;
+                        acc = a == 0 ? sd : __dadd_rn(acc, sd);
+                    }
+                    v[f] = __dadd_rn(u, __dmul_rn(acc, 0.25));
+                }
+        } else if (e.x < 0) {
+            const long long si = off[t] + e.y;
 #pragma unroll
             for (int f = 0; f < MAXNF; f++)
                 if (f < nf) {
@@ -296,6 +327,7 @@ __global__ void amr_ghost_kernel(double *U, int E, const long long *off, int nf,
                     v[f] = sum / 8.0;
                 }
         } else {
+            const long long si = off[t] + e.y;
 #pragma unroll
             for (int f = 0; f < MAXNF; f++)
                 if (f < nf)
@@ -306,7 +338,6 @@ __global__ void amr_ghost_kernel(double *U, int E, const long long *off, int nf,
             if (f < nf)
                 U[di + f * FS] = v[f];
     }
-    (void)flags;
 }
 
 // One flux correction at a coarse-fine face: the coarse cell's RHS entry d

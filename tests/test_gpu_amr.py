@@ -168,3 +168,56 @@ def test_amr_fill_bitwise_larger_edges(E):
     H.fill_ghosts(U)
     torch.cuda.synchronize()
     assert np.array_equal(U.cpu().numpy(), ref.U)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_linear_prolongation_fill_bitwise(periodic):
+    import torch
+    from paper_2210_06439_gb300 import binding
+    p = inputs.amr_box(periodic=periodic)
+    m = p.meta
+    ref = p.copy()
+    oracle.amr_ghost_fill(8, ref.off, ref.nf, m["level"], m["origin"], m["n0"], m["periodic"], ref.U, order=1)
+    H = binding.Hydro.from_problem(p)
+    H.set_prolongation(1)
+    U = torch.from_numpy(p.U).cuda()
+    for _ in range(2):
+        H.fill_ghosts(U)
+        torch.cuda.synchronize()
+        assert np.array_equal(U.cpu().numpy(), ref.U)
+    # back to injection: the plan is rebuilt
+    H.set_prolongation(0)
+    U = torch.from_numpy(p.U).cuda()
+    H.fill_ghosts(U)
+    torch.cuda.synchronize()
+    assert np.array_equal(U.cpu().numpy(), _oracle_fill(p).U)
+    with pytest.raises(binding.OctError):
+        H.set_prolongation(2)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_linear_prolongation_rk3_steps_match_oracle(precision):
+    import torch
+    from paper_2210_06439_gb300 import binding
+    p = inputs.amr_box()
+    m = p.meta
+    ref = p.copy()
+    oracle.amr_ghost_fill(8, ref.off, ref.nf, m["level"], m["origin"], m["n0"], m["periodic"], ref.U, order=1)
+    U0 = ref.U.copy()
+    dts = []
+    for _ in range(2):
+        dt, fired, st = oracle.rk3_step_amr(ref.edge, ref.off, ref.dx, ref.nf, ref.U, m["level"], m["origin"],
+                                            m["n0"], m["periodic"], gamma=ref.gamma, order=1)
+        assert st == 0 and fired == 0
+        dts.append(dt)
+    H = binding.Hydro.from_problem(p, precision=precision)
+    H.set_prolongation(1)
+    U = torch.from_numpy(U0).cuda()
+    st = torch.cuda.Stream()
+    dg = [H.rk_step(U, stream=st) for _ in range(2)]
+    torch.cuda.synchronize()
+    assert H.error_flags() == 0
+    np.testing.assert_allclose(dg, dts, rtol=1e-12 if precision == 0 else MIXED_SPEED_RTOL)
+    got = U.cpu().numpy()
+    errs = field_errors(interior_layout(got, p), interior_layout(ref.U, p), p.nf, e3s(p))
+    assert np.all(errs <= (1e-12 if precision == 0 else 1e-6)), errs
