@@ -445,6 +445,29 @@ def sedov_blast(nsub: int = 8, E: int = 8, e_blast: float = 1.0, rho0: float = 1
                         meta=dict(e_blast=e_blast, rho0=rho0))
 
 
+def amr_wave(n_coarse: int = 4, E: int = 8, amp: float = 0.2) -> Problem:
+    """The two-level geometry of amr_box (periodic) filled with a smooth
+    density wave rho = 1 + amp sin 2 pi x advected at v = (1, 0, 0), p = 1,
+    one species equal to rho: the wave crosses the coarse-fine faces.  Values
+    are taken at cell centres.  meta as amr_box, plus amp."""
+    q = amr_box(seed=1, n_coarse=n_coarse, E=E, n_species=1, periodic=True)
+    B = E + 2 * NG
+    i = np.arange(E)
+    lev, org = q.meta["level"], q.meta["origin"]
+    q.U[:] = 0.0
+    for k in range(q.n_sub):
+        h = float(q.dx[k])
+        zz, yy, xx = np.meshgrid((org[k, 2] + i + 0.5) * h, (org[k, 1] + i + 0.5) * h, (org[k, 0] + i + 0.5) * h,
+                                 indexing="ij")
+        rho = 1.0 + amp * np.sin(2.0 * math.pi * xx)
+        one = np.ones_like(rho)
+        f = conserved(rho, one, 0.0 * one, 0.0 * one, one, [rho.copy()])
+        q.U[q.off[k]: q.off[k] + q.nf * B ** 3].reshape(q.nf, B, B, B)[:, NG:NG + E, NG:NG + E, NG:NG + E] = f
+    q.name = f"amr_wave_{n_coarse * E}"
+    q.meta["amp"] = amp
+    return q
+
+
 def amr_box(seed: int = 1006, n_coarse: int = 4, E: int = 8, n_species: int = 5, periodic: bool = True) -> Problem:
     """Two refinement levels in the unit box (Sec. II "Data-Structure": an
     adaptive octree with a subgrid per leaf): n_coarse^3 level-0 subgrids of
