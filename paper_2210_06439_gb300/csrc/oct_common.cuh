@@ -39,7 +39,7 @@ struct GroupTab {
     int napt;                      // face points per face (the same for every axis of the group)
     signed char apt[3][4];         // indices into the point arrays, per face axis
 };
-constexpr int NGROUPS = 7;
+constexpr int NGROUPS = 5;
 
 struct RhsArgs {
     const double *U;

@@ -357,16 +357,15 @@ __device__ __forceinline__ int cidx(int i, int j, int tx, int ty)
 }
 
 // Compile-time line geometry of group g (the same grouping as the host's
-// table): 0 x, 1 y, 2 z, 3 xy diagonals, 4 xz, 5 yz, 6 body diagonals.
-__host__ __device__ constexpr int gnl(int g) { return g < 3 ? 1 : (g < 6 ? 2 : 4); }
+// table): 0 the three axis lines x, y, z; 1 xy diagonals; 2 xz; 3 yz;
+// 4 body diagonals.
+__host__ __device__ constexpr int gnl(int g) { return g == 0 ? 3 : (g < 4 ? 2 : 4); }
 __host__ __device__ constexpr int gline(int g, int l, int a)
 {
-    return g == 0   ? (a == 0 ? 1 : 0)
-           : g == 1 ? (a == 1 ? 1 : 0)
-           : g == 2 ? (a == 2 ? 1 : 0)
-           : g == 3 ? (a == 0 ? 1 : a == 1 ? (l == 0 ? 1 : -1) : 0)
-           : g == 4 ? (a == 0 ? 1 : a == 2 ? (l == 0 ? 1 : -1) : 0)
-           : g == 5 ? (a == 1 ? 1 : a == 2 ? (l == 0 ? 1 : -1) : 0)
+    return g == 0   ? (a == l ? 1 : 0)
+           : g == 1 ? (a == 0 ? 1 : a == 1 ? (l == 0 ? 1 : -1) : 0)
+           : g == 2 ? (a == 0 ? 1 : a == 2 ? (l == 0 ? 1 : -1) : 0)
+           : g == 3 ? (a == 1 ? 1 : a == 2 ? (l == 0 ? 1 : -1) : 0)
                     : (a == 0 ? 1 : a == 1 ? ((l == 0 || l == 3) ? 1 : -1) : ((l == 0 || l == 2) ? 1 : -1));
 }
 
@@ -392,21 +391,28 @@ __device__ __forceinline__ void phase_a(T *temp, const float *raw, const double 
                                         int tid)
 {
     constexpr int NL = gnl(G);
-    constexpr int LX = gline(G, 0, 0) != 0, LY = gline(G, 0, 1) != 0;
-    const int t = inplane ? (LX | (LY << 1)) : 0;
-    const int n = nlist[t];
-    const unsigned mg = magic[t];
-    const int per = n * nf;
-    const int *lst = lists + t * NC;
-    for (int q = tid; q < NL * per; q += NT) {
+    // per line: its cell list (the x / y ring only for lines with a nonzero x /
+    // y step, in planes that own x / y faces) and its item count; lines without
+    // a z step have nothing to do in the boundary planes
+    int beg[NL + 1];
+    beg[0] = 0;
+    sfor<NL>([&](auto Lc) {
+        constexpr int L = decltype(Lc)::value;
+        constexpr int t = (gline(G, L, 0) != 0) | ((gline(G, L, 1) != 0) << 1);
+        const int n = inplane ? nlist[t] : (gline(G, L, 2) != 0 ? nlist[0] : 0);
+        beg[L + 1] = beg[L] + n * nf;
+    });
+    for (int q = tid; q < beg[NL]; q += NT) {
         sfor<NL>([&](auto Lc) {
             constexpr int L = decltype(Lc)::value;
-            if (q >= L * per && q < (L + 1) * per) {
+            if (q >= beg[L] && q < beg[L + 1]) {
                 constexpr int dx = gline(G, L, 0), dy = gline(G, L, 1), dz = gline(G, L, 2);
-                const int r = q - L * per;
-                const int f = __umulhi((unsigned)r, mg);
+                const int t = inplane ? ((dx != 0) | ((dy != 0) << 1)) : 0;
+                const int n = nlist[t];
+                const int r = q - beg[L];
+                const int f = __umulhi((unsigned)r, magic[t]);
                 const int c = r - f * n;
-                const int info = lst[c];
+                const int info = lists[t * NC + c];
                 const int i = (info & 0xFF) - 1, j = ((info >> 8) & 0xFF) - 1, ci = info >> 16;
                 T u[5];
                 if constexpr (STAGED) {
@@ -568,7 +574,6 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                           t3 = nl > 3 ? ltype(3) : 0;
                 const int n0 = nlist[t0], n1 = nl > 1 ? nlist[t1] : 0, n2 = nl > 2 ? nlist[t2] : 0,
                           n3 = nl > 3 ? nlist[t3] : 0;
-                const int totA = (n0 + n1 + n2 + n3) * nf;
                 // ---- phase A: 1-D PPM for every (line, field, cell) of the group ----
                 switch (g) {
 #define OCT_PHASE_A(GG)                                                                                              \
@@ -581,8 +586,6 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                     OCT_PHASE_A(2)
                     OCT_PHASE_A(3)
                     OCT_PHASE_A(4)
-                    OCT_PHASE_A(5)
-                    OCT_PHASE_A(6)
 #undef OCT_PHASE_A
                 }
                 __syncthreads();
@@ -592,8 +595,12 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                 // the inward end of ring cells ----
                 {
                     const int per_in = inplane ? 2 * ncin : ncin;
-                    const int m0 = per_in + (n0 - ncin), m1 = nl > 1 ? per_in + (n1 - ncin) : 0,
-                              m2 = nl > 2 ? per_in + (n2 - ncin) : 0, m3 = nl > 3 ? per_in + (n3 - ncin) : 0;
+                    // points of each line; in the boundary planes only lines with a z step
+                    auto mline = [&](int l, int nl_) -> int {
+                        return (!inplane && G.line[l][2] == 0) ? 0 : per_in + (nl_ - ncin);
+                    };
+                    const int m0 = mline(0, n0), m1 = nl > 1 ? mline(1, n1) : 0, m2 = nl > 2 ? mline(2, n2) : 0,
+                              m3 = nl > 3 ? mline(3, n3) : 0;
                     const int tot = m0 + m1 + m2 + m3;
                     for (int q = tid; q < tot; q += NT) {
                         int l = 0, r = q, t = t0;
