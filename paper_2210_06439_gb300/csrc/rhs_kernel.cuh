@@ -2,7 +2,8 @@
 // instantiated for FP64 and for the mixed form).
 //
 // Method (Octo-Tiger hydro solver, arXiv 2210.06439 Sec. II "Solvers"):
-// PPM reconstruction of every conserved field to the 26 points of each cell
+// PPM reconstruction of every conserved field (or, on request, of the
+// primitive variables) to the 26 points of each cell
 // (6 face centres, 12 edge midpoints, 8 corners; the value at x + d/2 comes
 // from 1-D PPM along the cells x + m d), the Kurganov-Tadmor flux at the 9
 // Newton-Cotes (tensor Simpson) points of every face with a local speed per
@@ -10,18 +11,20 @@
 //
 // GPU organisation.  A CTA owns one work item: a tx * ty column of a subgrid
 // (tx, ty <= 8) and streams through its z planes kz = -1 .. E.  For each plane
-// the 13 lines are processed in 7 groups (x, y, z, xy, xz, yz, body
-// diagonals); within a group both sides of each face quadrature point are
-// available, so the flux of that point is formed as soon as the group's point
-// values exist and no plane ever holds all 26 points of all fields:
+// the 13 lines are processed in 5 groups (the axis lines x, y, z; the xy,
+// xz and yz diagonals; the body diagonals); within a group both sides of each
+// face quadrature point are available, so the flux of that point is formed as
+// soon as the group's point values exist and no plane ever holds all 26
+// points of all fields:
 //   phase A  every (line, cell, field) of the group: 1-D PPM -> both ends
 //            into the group buffer (shared memory);
-//   phase B  one thread per face: the group's quadrature points of that face,
+//   phase B1 (FP64) the primitives of every needed point, once;
+//   phase B2 one thread per face: the group's quadrature points of that face,
 //            primitives on both sides, KT flux, Simpson-weighted sum into the
 //            face accumulator; the z faces below the plane take their L side
 //            from the +z ends the previous plane left in the saved buffer, and
 //            the same thread then replaces those with this plane's +z ends.
-// After the 7 groups the in-plane (x, y) face fluxes are complete; the
+// After the 5 groups the in-plane (x, y) face fluxes are complete; the
 // divergence of a plane is finished one plane later, once its upper z face
 // is known.  The signal speed max over all face points is reduced per item.
 #pragma once
