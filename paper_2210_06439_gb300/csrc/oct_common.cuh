@@ -36,10 +36,11 @@ struct GroupTab {
     int nzp;                       // +z ends this group leaves for the next plane
     signed char zp_src[4], zp_dst[4];
     int has[3];                    // group has lines with a nonzero x / y / z step
-    int napt;                      // face points per face (the same for every axis of the group)
+    int napt;                      // face points per face, the most over the axes
+    int nax[3];                    // face points per face of each axis
     signed char apt[3][4];         // indices into the point arrays, per face axis
 };
-constexpr int NGROUPS = 5;
+constexpr int NGROUPS = 4;
 
 struct RhsArgs {
     const double *U;

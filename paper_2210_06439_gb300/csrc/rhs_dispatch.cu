@@ -15,15 +15,15 @@ static void canon(const int *d, int *line, int *end)
     *end = first > 0 ? 1 : 0;
 }
 
-// The 13 PPM lines in 5 groups (the axis lines x, y, z; the xy, xz and yz
-// diagonals; the body diagonals) and,
+// The 13 PPM lines in 4 groups (the axis lines x, y, z; the xy and xz
+// diagonals; the yz diagonals; the body diagonals) and,
 // per group, its face quadrature points, per-axis point lists and the +z ends
 // it carries to the next plane (see rhs_kernel.cuh).
 bool build_group_tables(GroupTab *gs)
 {
     static const int L[13][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1},
                                  {0, 1, 1}, {0, 1, -1}, {1, 1, 1}, {1, -1, -1}, {1, -1, 1}, {1, 1, -1}};
-    static const int GL[NGROUPS][5] = {{3, 0, 1, 2}, {2, 3, 4}, {2, 5, 6}, {2, 7, 8}, {4, 9, 10, 11, 12}};
+    static const int GL[NGROUPS][5] = {{3, 0, 1, 2}, {4, 3, 4, 5, 6}, {2, 7, 8}, {4, 9, 10, 11, 12}};
     for (int g = 0; g < NGROUPS; g++) {
         GroupTab &G = gs[g];
         memset(&G, 0, sizeof G);
@@ -68,8 +68,7 @@ bool build_group_tables(GroupTab *gs)
         }
         G.napt = cnt[0] > cnt[1] ? (cnt[0] > cnt[2] ? cnt[0] : cnt[2]) : (cnt[1] > cnt[2] ? cnt[1] : cnt[2]);
         for (int k = 0; k < 3; k++)
-            if (cnt[k] != 0 && cnt[k] != G.napt)
-                return false;  // the uniform point loop of the kernel needs equal counts
+            G.nax[k] = cnt[k];
         for (int l = 0; l < G.nl; l++) {
             if (!G.line[l][2])
                 continue;

@@ -11,8 +11,8 @@
 //
 // GPU organisation.  A CTA owns one work item: a tx * ty column of a subgrid
 // (tx, ty <= 8) and streams through its z planes kz = -1 .. E.  For each plane
-// the 13 lines are processed in 5 groups (the axis lines x, y, z; the xy,
-// xz and yz diagonals; the body diagonals); within a group both sides of each
+// the 13 lines are processed in 4 groups (the axis lines x, y, z; the xy and
+// xz diagonals; the yz diagonals; the body diagonals); within a group both sides of each
 // face quadrature point are available, so the flux of that point is formed as
 // soon as the group's point values exist and no plane ever holds all 26
 // points of all fields:
@@ -24,7 +24,7 @@
 //            face accumulator; the z faces below the plane take their L side
 //            from the +z ends the previous plane left in the saved buffer, and
 //            the same thread then replaces those with this plane's +z ends.
-// After the 5 groups the in-plane (x, y) face fluxes are complete; the
+// After the 4 groups the in-plane (x, y) face fluxes are complete; the
 // divergence of a plane is finished one plane later, once its upper z face
 // is known.  The signal speed max over all face points is reduced per item.
 #pragma once
@@ -360,15 +360,14 @@ __device__ __forceinline__ int cidx(int i, int j, int tx, int ty)
 }
 
 // Compile-time line geometry of group g (the same grouping as the host's
-// table): 0 the three axis lines x, y, z; 1 xy diagonals; 2 xz; 3 yz;
-// 4 body diagonals.
-__host__ __device__ constexpr int gnl(int g) { return g == 0 ? 3 : (g < 4 ? 2 : 4); }
+// table): 0 the three axis lines x, y, z; 1 the xy and xz diagonals; 2 the yz
+// diagonals; 3 the body diagonals.
+__host__ __device__ constexpr int gnl(int g) { return g == 0 ? 3 : (g == 2 ? 2 : 4); }
 __host__ __device__ constexpr int gline(int g, int l, int a)
 {
     return g == 0   ? (a == l ? 1 : 0)
-           : g == 1 ? (a == 0 ? 1 : a == 1 ? (l == 0 ? 1 : -1) : 0)
-           : g == 2 ? (a == 0 ? 1 : a == 2 ? (l == 0 ? 1 : -1) : 0)
-           : g == 3 ? (a == 1 ? 1 : a == 2 ? (l == 0 ? 1 : -1) : 0)
+           : g == 1 ? (a == 0 ? 1 : a == 1 ? (l == 0 ? 1 : l == 1 ? -1 : 0) : (l == 2 ? 1 : l == 3 ? -1 : 0))
+           : g == 2 ? (a == 1 ? 1 : a == 2 ? (l == 0 ? 1 : -1) : 0)
                     : (a == 0 ? 1 : a == 1 ? ((l == 0 || l == 3) ? 1 : -1) : ((l == 0 || l == 2) ? 1 : -1));
 }
 
@@ -588,7 +587,6 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                     OCT_PHASE_A(1)
                     OCT_PHASE_A(2)
                     OCT_PHASE_A(3)
-                    OCT_PHASE_A(4)
 #undef OCT_PHASE_A
                 }
                 __syncthreads();
@@ -681,8 +679,8 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                 __syncthreads();
                 }
                 // ---- phase B2: KT flux at the group's points, one thread per face;
-                // the faces of the group's axes packed densely (every face of the
-                // group has the same number of points, so the point loop is uniform) ----
+                // the faces of the group's axes packed densely, each looping over
+                // its axis's points of the group ----
                 {
                     const int nfx = (inplane && G.has[0]) ? (tx + 1) * ty : 0;
                     const int nfy = (inplane && G.has[1]) ? tx * (ty + 1) : 0;
@@ -711,7 +709,8 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                         for (int f = 0; f < MAXNF; f++)
                             acc[f] = T(0);
                         T pacc = T(0);
-                        for (int k = 0; k < G.napt; k++) {
+                        const int npa = axis == 0 ? G.nax[0] : (axis == 1 ? G.nax[1] : G.nax[2]);
+                        for (int k = 0; k < npa; k++) {
                             const int pt = G.apt[axis][k];
                             // half the Simpson weight (16, 4 or 1)/36
                             const T hw = G.wcls[pt] == 0 ? T(8.0 / 36.0) : (G.wcls[pt] == 1 ? T(2.0 / 36.0) : T(0.5 / 36.0));
