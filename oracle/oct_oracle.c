@@ -103,17 +103,23 @@ void oco_ppm(const double *u, double *um_out, double *up_out)
     double u0 = u[2];
     double up = 0.5 * (u[2] + u[3]) - (dp - d0) / 6.0;
     double um = 0.5 * (u[1] + u[2]) - (d0 - dm) / 6.0;
-    if ((up - u0) * (u0 - um) <= 0.0) {
-        /* local extremum: flat profile */
+    /* The constraints are conditions on signs and on ratios of magnitudes,
+     * the same at every scale of u; they are written without products of two
+     * differences, which underflow for |u| below about 1e-154. */
+    if (!((up - u0 > 0.0 && u0 - um > 0.0) || (up - u0 < 0.0 && u0 - um < 0.0))) {
+        /* local extremum, (up - u0)(u0 - um) <= 0: flat profile */
         um = u0;
         up = u0;
     } else {
+        /* overshoot: du (u0 - (up + um)/2) > du^2/6, or < -du^2/6; divided
+         * by |du| > 0 these read 6 sgn(du) x > |du| and < -|du| */
         double du = up - um;
-        double m6 = du * (u0 - 0.5 * (up + um));
-        double dd = du * du / 6.0;
-        if (m6 > dd)
+        double x = u0 - 0.5 * (up + um);
+        double t = du > 0.0 ? 6.0 * x : -6.0 * x;
+        double a = fabs(du);
+        if (t > a)
             um = 3.0 * u0 - 2.0 * up;
-        else if (-dd > m6)
+        else if (t < -a)
             up = 3.0 * u0 - 2.0 * um;
     }
     *um_out = um;

@@ -97,6 +97,22 @@ def test_ppm_odd_and_reversal_symmetry_bitwise():
         assert (rm, rp) == (up, um)
 
 
+
+def test_ppm_scale_invariant_bitwise():
+    """The reconstruction is positively homogeneous: PPM of 2^k u is 2^k times
+    PPM of u, bit for bit, from 2^-900 to 2^900 (every operation scales
+    exactly while no intermediate leaves the normal range).  A limiter or
+    monotonicity test written on products of two differences fails this at
+    small scales, where such products underflow to zero."""
+    rng = np.random.default_rng(19)
+    for _ in range(2000):
+        u = rng.standard_normal(5)
+        um, up = oracle.ppm(u)
+        for k in (-900, -700, -520, -300, 0, 300, 700, 900):
+            sm, sp = oracle.ppm(np.ldexp(u, k))
+            assert (sm, sp) == (math.ldexp(um, k), math.ldexp(up, k)), (u, k)
+
+
 # --------------------------------------------------------------------------
 # Point primitives, KT flux and the face quadrature
 # --------------------------------------------------------------------------
