@@ -161,4 +161,42 @@ __device__ __forceinline__ double rcp_nr(double x)
     return fma(r, e, r);
 }
 
+// tau^gamma, the internal energy that the entropy tracer gives where the
+// dual-energy switch selects it.  For gamma = 5/3 (the ideal monatomic gas of
+// every workload here): with tau = m 2^(3k), m in [1, 8) (exact, on the
+// exponent field), tau^(5/3) = m^(5/3) 2^(5k), and y = m^(5/3) solves
+// y^3 = m^5.  An FP32 estimate y0 = 2^(5/3 log2 m) (the hardware log2 and
+// exp2 approximations; relative error below 1e-6) is refined by two Newton
+// steps y <- y - (y^3 - m^5) r in FP64, r = 1/(3 y0^2) from FP32: each step
+// multiplies the relative error by max(error, error of r), about 1e-6, so the
+// result is within a few ulp.  Nine FP64 operations instead of a pow.  Other
+// gamma, tau <= 0, tau outside [2^-600, 2^601) and inf or NaN: pow, in a call
+// of its own so that warps without such a point do not issue it.
+static __device__ __noinline__ double pow_rare(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ double eint_of_tau(double tau, double gamma)
+{
+    const int th = __double2hiint(tau);
+    const int eb = (th >> 20) - 1023;  // unbiased exponent (th > 0: positive)
+    if (__double_as_longlong(gamma) != __double_as_longlong(5.0 / 3.0) || th <= 0 || eb < -600 || eb > 600)
+        return pow_rare(tau, gamma);
+    // k = floor(eb / 3), j = eb - 3k in {0, 1, 2}
+    const int k = (eb >= 0 ? eb : eb - 2) / 3;
+    const int j = eb - 3 * k;
+    const double m = __hiloint2double((th & 0x000FFFFF) | ((j + 1023) << 20), __double2loint(tau));
+    const double m2 = m * m;
+    const double T = m2 * m2 * m;
+    float mf;
+    d2f_est(m, mf);
+    float lf, yf, rf;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lf) : "f"(mf));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(lf * (5.0f / 3.0f)));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(3.0f * yf * yf));
+    const double r = f2d_normal(rf);
+    double y = f2d_normal(yf);
+    y = fma(-fma(y * y, y, -T), r, y);
+    y = fma(-fma(y * y, y, -T), r, y);
+    // y in [1, 32): scale by 2^(5k) on the exponent field (the result stays normal)
+    return __hiloint2double(__double2hiint(y) + 5 * k * (1 << 20), __double2loint(y));
+}
+
 }  // namespace octh

@@ -256,7 +256,7 @@ __device__ __forceinline__ void prim_point(const double *q, double gamma, double
     double ei = fma(-0.5, sv, q[F_EGAS]);
     double c2;
     if (ei < eps1 * q[F_EGAS]) {
-        ei = pow(q[F_TAU], gamma);
+        ei = eint_of_tau(q[F_TAU], gamma);
         p = gm1 * ei;
         c2 = gamma * p * ir;
     } else {

@@ -398,7 +398,7 @@ __global__ void prim_cells_kernel(const double *U, double *W, const int *edge, c
         const double vx = sx * ir, vy = sy * ir, vz = sz * ir;
         double ei = fma(-0.5, fma(sz, vz, fma(sy, vy, sx * vx)), E);
         if (ei < eps1 * E)
-            ei = pow(tau, gamma);
+            ei = eint_of_tau(tau, gamma);
         const double p = (gamma - 1.0) * ei;
         w[c] = rho;
         w[FS + c] = vx;

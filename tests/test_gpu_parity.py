@@ -234,3 +234,46 @@ def test_dt_cap_applies_to_replayed_graphs():
 def test_species_counts(n_species, precision):
     """Field counts other than 11: no species (6 fields), one and three."""
     _check_rhs(inputs.periodic_box(nsub=2, n_species=n_species), precision)
+
+
+@pytest.mark.parametrize("recon", [0, 1])
+def test_dual_energy_switch_over_wide_tau_range(recon):
+    """Velocities 2000 times those of the noisy gas law (kinetic energy about
+    1e5 times the internal one), so that the dual-energy switch takes
+    e_int = tau^gamma at (nearly) every point, with each subgrid's tau scaled
+    by its own power of two from 2^-640 to 2^299: the
+    cheap tau^(5/3) of the FP64 kernels against the oracle's pow, per
+    subgrid, on both sides of the exponent limits of its fast path (2^+-600;
+    beyond them the kernels call pow as well)."""
+    torch = _torch()
+    from paper_2210_06439_gb300 import binding
+    p = inputs.mixed_levels(n=9)
+    shifts = [-640, -601, -598, -200, -1, 0, 5, 150, 299]
+    nf = p.nf
+    for s in range(p.n_sub):
+        B = int(p.edge[s]) + 6
+        blk = p.U[p.off[s]: p.off[s] + nf * B ** 3].reshape(nf, -1)
+        rho = blk[0]
+        kin = 0.5 * (blk[1] ** 2 + blk[2] ** 2 + blk[3] ** 2) / rho
+        eint = blk[4] - kin
+        blk[1:4] *= 2000.0
+        blk[4] = eint + 0.5 * (blk[1] ** 2 + blk[2] ** 2 + blk[3] ** 2) / rho
+        assert np.mean(eint < 1e-3 * blk[4]) > 0.999
+        blk[5] *= 2.0 ** shifts[s]
+    d_o, am_o, nb = oracle.rhs(p.edge, p.off, p.dx, nf, p.U, nthreads=0, recon=recon)
+    assert nb == 0
+    H = binding.Hydro.from_problem(p, precision=0, recon=recon)
+    U = torch.from_numpy(p.U).cuda()
+    d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+    am = torch.zeros(p.n_sub, dtype=torch.float64, device="cuda")
+    H.rhs(U, d, am)
+    torch.cuda.synchronize()
+    assert H.error_flags() == 0
+    d_g = d.cpu().numpy()
+    o = 0
+    for s in range(p.n_sub):
+        E3 = int(p.edge[s]) ** 3
+        errs = field_errors(d_g[o: o + nf * E3], d_o[o: o + nf * E3], nf, [E3])
+        assert np.all(errs <= 1e-12), (s, shifts[s], errs)
+        o += nf * E3
+    np.testing.assert_allclose(am.cpu().numpy(), am_o, rtol=1e-12)
