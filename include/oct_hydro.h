@@ -52,7 +52,10 @@
  * default stream).  Only the calls that return a value to the host
  * (oct_hydro_max_dt, oct_hydro_rk_step with a non-NULL dt pointer,
  * oct_hydro_get_error_flags, the *_host calls) synchronise that stream.
- * A handle is not thread-safe: one host thread at a time per handle.
+ * A handle is not thread-safe: one host thread at a time per handle.  Its
+ * scratch buffers and the RHS kernel's scheduling counters are per handle,
+ * so work on one handle must not overlap on the GPU: issue it on one stream,
+ * or order the streams with events.
  *
  * Device: a handle belongs to the device that is current at
  * oct_hydro_create; every call on it makes that device current for its
@@ -218,9 +221,10 @@ oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int n_steps, d
 oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_host, void *cuda_stream);
 
 /* Times the candidate launch shapes of the RHS kernel on U_sample -- tile
- * capacity and threads (8x8 cells per work item with 256 or 512 threads, or
- * 8x4 with 256) x resident CTAs per SM (1 up to the occupancy limit) -- and keeps the fastest for this layout, precision
- * and reconstruction choice.  Drops captured graphs.  When the environment
+ * capacity and threads (8x8 cells per work item with 256, 512 or 1024
+ * threads, or 8x4 with 256) x resident CTAs per SM (1 up to the occupancy
+ * limit) -- and keeps the fastest for this layout, precision and
+ * reconstruction choice.  Drops captured graphs.  When the environment
  * variable OCT_HYDRO_TUNE_CACHE names a file, a result stored there for the
  * same GPU model, SM count, form, field count and edge counts is applied
  * without trial launches, and a new result is appended (one text line per
@@ -258,8 +262,11 @@ oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_species, dou
 /* Launch shape of the RHS kernel for the current layout and precision
  * (the paper's Sec. V-B splits big kernels into tasks for the same reason:
  * enough independent work per core): tile mode (0: 8x8-cell columns with
- * 256 threads, 1: 8x4 with 256, 2: 8x8 with 512), CTAs resident per SM, and
- * work items.  Any pointer may be NULL. */
+ * 256 threads, 1: 8x4 with 256, 2: 8x8 with 512, 3: 8x8 with 1024), CTAs
+ * resident per SM, and work items.  The items are the tiles of every
+ * subgrid, the last round's tiles cut in half along y when they would leave
+ * at least half the persistent grid idle; CTAs draw items in order of
+ * decreasing work from a counter on the device.  Any pointer may be NULL. */
 oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *ctas_per_sm, int *n_items);
 
 /* Reads and clears the device error flags (OCT_FLAG_*); synchronises. */

@@ -1,9 +1,9 @@
 """Builds the sm_103a CUDA library liboct_hydro.so in-tree with nvcc.
 
-The four RHS kernel instances (FP64 / mixed, tile capacity 8x8 / 8x4) are
-separate translation units; they and the host side compile in parallel to
-objects, which nvcc then links into one shared library (static CUDA
-runtime).  Only compute_103a/sm_103a code is generated."""
+The sixteen RHS kernel instances (FP64 / mixed form, four launch shapes,
+conserved or primitive reconstruction) are separate translation units; they
+and the host side compile in parallel to objects, which nvcc then links into
+one shared library (static CUDA runtime).  Only compute_103a/sm_103a code is generated."""
 from __future__ import annotations
 
 import os
@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboct_hydro.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include", "oct_hydro.h")
 UNITS = ["oct_hydro.cu", "rhs_dispatch.cu"] + [f"rhs_{form}_m{mode}{rec}.cu" for rec in ("", "_prim")
-                                              for form in ("fp64", "mixed") for mode in (0, 1, 2)]
+                                              for form in ("fp64", "mixed") for mode in (0, 1, 2, 3)]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]

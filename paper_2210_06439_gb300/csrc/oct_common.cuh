@@ -61,6 +61,11 @@ struct RhsArgs {
     // [face 2k+side][f][t2][t1] with (t1, t2) its other axes in increasing order
     double *faces;
     const int *face_slot;
+    // execution order of the items (null: in index order) and the ticket
+    // counter of dynamic scheduling ([0] next ticket, [1] CTAs done; both zero
+    // between launches; null: static round robin)
+    const int *order;
+    int *ticket;
 };
 
 // ---------------------------------------------------------------------------

@@ -76,10 +76,12 @@ struct oct_hydro {
     std::vector<int> nbr;
     std::vector<WorkItem> items;
     std::vector<int> item_begin;
+    std::vector<int> order;             // execution order of the items (empty: index order)
+    int items_mode = -1, items_grid = 0;  // the launch shape the items were cut for
     std::vector<long long> cell_begin;  // packed interior-cell offset of each subgrid
     long long state_len = 0, rhs_len = 0;
     // launch shape: 0 8x8 tiles (6x6 for edge 12), 256 threads; 1 8x4 tiles (6x4
-    // for edge 12), 256 threads; 2 8x8 tiles, 512 threads
+    // for edge 12), 256 threads; 2 8x8 tiles, 512 threads; 3 8x8 tiles, 1024 threads
     int tile_mode = 0;
     // [form][tile mode], form = precision + 2 * recon
     int ctas_per_sm[4][RHS_MODES] = {};  // the occupancy limit (0: the shape does not fit)
@@ -91,6 +93,8 @@ struct oct_hydro {
     long long *d_off = nullptr, *d_doff = nullptr, *d_cell_begin = nullptr;
     double *d_dx = nullptr;
     WorkItem *d_items = nullptr;
+    int *d_order = nullptr;   // execution order (null: index order)
+    int *d_ticket = nullptr;  // dynamic-scheduling counters of the RHS kernel (zero between launches)
     double *d_dtcap = nullptr;  // dt cap of oct_hydro_rk_step (0: none), read by the captured graph
     double *d_amax_tile = nullptr, *d_dt = nullptr, *d_W = nullptr, *d_L = nullptr, *d_Uhost = nullptr,
            *d_Lhost = nullptr;
@@ -151,6 +155,7 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_cell_begin);
     dfree(h->d_dx);
     dfree(h->d_items);
+    dfree(h->d_order);
     dfree(h->d_amax_tile);
     dfree(h->d_W);
     dfree(h->d_L);
@@ -184,26 +189,74 @@ static oct_status set_kernel_attrs(oct_hydro *h)
 
 static int form_of(const oct_hydro *h) { return h->precision + 2 * h->recon; }
 
+// CTAs of the persistent RHS grid for the current form and launch shape.
+static int grid_ctas(const oct_hydro *h)
+{
+    const int form = form_of(h), mode = h->tile_mode;
+    const int per_sm = h->cta_use[form][mode] > 0 ? h->cta_use[form][mode] : h->ctas_per_sm[form][mode];
+    return h->n_sm * std::max(per_sm, 1);
+}
+
+// Work items for the current launch shape.  Each subgrid is cut into tiles of
+// the shape's capacity (6 wide for edge 12).  When the tiles are all of one
+// size and do not fill the last round of the persistent grid -- r = N mod G
+// items left over for G CTAs, r at most G/2 -- the last r tiles are cut in
+// half along y: the last round then runs 2r half tiles (each a little over
+// half the work of a tile: the ring of halo cells grows) instead of r whole
+// tiles while G - r CTAs wait.  With mixed sizes the execution order is by
+// estimated work, largest first, and the kernel hands out items dynamically.
+// A subgrid's items stay contiguous (item_begin).
 static void build_items(oct_hydro *h)
 {
+    const int G = grid_ctas(h);
     h->items.clear();
+    h->order.clear();
     h->item_begin.assign(h->n_sub + 1, 0);
+    bool same = true;
+    long long n_tiles = 0;
+    for (int s = 0; s < h->n_sub; s++) {
+        const int E = h->edge[s];
+        const int tx = (E == 12) ? 6 : 8, ty = (h->tile_mode == 1) ? 4 : tx;
+        n_tiles += (long long)(E / tx) * (E / ty);
+        same = same && E == h->edge[0];
+    }
+    const int ty0 = (h->tile_mode == 1) ? 4 : (h->edge[0] == 12 ? 6 : 8);
+    const long long r = n_tiles % G;
+    const long long split_from = (same && r > 0 && 2 * r <= G && ty0 % 2 == 0) ? n_tiles - r : n_tiles;
+    long long k = 0;
     for (int s = 0; s < h->n_sub; s++) {
         h->item_begin[s] = (int)h->items.size();
-        int E = h->edge[s];
-        int tx = (E == 12) ? 6 : 8;
-        int ty = (h->tile_mode == 1) ? 4 : tx;  // modes 0 and 2 share the 8x8 tiles
+        const int E = h->edge[s];
+        const int tx = (E == 12) ? 6 : 8;
+        const int ty = (h->tile_mode == 1) ? 4 : tx;
         for (int y0 = 0; y0 < E; y0 += ty)
-            for (int x0 = 0; x0 < E; x0 += tx) {
-                WorkItem w;
-                w.s = s;
-                w.x0 = x0;
-                w.y0 = y0;
-                w.txty = tx | (ty << 8);
-                h->items.push_back(w);
+            for (int x0 = 0; x0 < E; x0 += tx, k++) {
+                const int parts = k >= split_from ? 2 : 1;
+                for (int p = 0; p < parts; p++) {
+                    WorkItem w;
+                    w.s = s;
+                    w.x0 = x0;
+                    w.y0 = y0 + p * (ty / parts);
+                    w.txty = tx | ((ty / parts) << 8);
+                    h->items.push_back(w);
+                }
             }
     }
     h->item_begin[h->n_sub] = (int)h->items.size();
+    if (!same) {
+        // largest first: cells plus the halo ring, times the planes
+        auto work = [&](const WorkItem &w) {
+            const int tx = w.txty & 0xFF, ty = (w.txty >> 8) & 0xFF;
+            return (long long)(tx * ty + tx + ty) * (h->edge[w.s] + 2);
+        };
+        h->order.resize(h->items.size());
+        for (size_t i = 0; i < h->items.size(); i++)
+            h->order[i] = (int)i;
+        std::stable_sort(h->order.begin(), h->order.end(),
+                         [&](int a, int b) { return work(h->items[a]) > work(h->items[b]); });
+    }
+    h->items_mode = h->tile_mode;
+    h->items_grid = G;
 }
 
 static oct_status upload_items(oct_hydro *h)
@@ -211,13 +264,31 @@ static oct_status upload_items(oct_hydro *h)
     dfree(h->d_items);
     dfree(h->d_item_begin);
     dfree(h->d_amax_tile);
+    dfree(h->d_order);
     CUDA_TRY(cudaMalloc(&h->d_items, sizeof(WorkItem) * h->items.size()));
     CUDA_TRY(cudaMemcpy(h->d_items, h->items.data(), sizeof(WorkItem) * h->items.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&h->d_item_begin, sizeof(int) * h->item_begin.size()));
     CUDA_TRY(cudaMemcpy(h->d_item_begin, h->item_begin.data(), sizeof(int) * h->item_begin.size(),
                         cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&h->d_amax_tile, sizeof(double) * std::max<size_t>(1, h->items.size())));
+    if (!h->order.empty()) {
+        CUDA_TRY(cudaMalloc(&h->d_order, sizeof(int) * h->order.size()));
+        CUDA_TRY(cudaMemcpy(h->d_order, h->order.data(), sizeof(int) * h->order.size(), cudaMemcpyHostToDevice));
+    }
     return OCT_OK;
+}
+
+// Re-cuts the work items when the launch shape or the grid changed since they
+// were built (precision, reconstruction or autotuning); captured step graphs
+// hold the old items and are dropped.  Called before any RHS launch, outside
+// graph capture.
+static oct_status sync_items(oct_hydro *h)
+{
+    if (h->items_mode == h->tile_mode && h->items_grid == grid_ctas(h))
+        return OCT_OK;
+    build_items(h);
+    drop_graphs(h);
+    return upload_items(h);
 }
 
 static bool valid_edge(int E)
@@ -267,6 +338,10 @@ extern "C" oct_status oct_hydro_create(int n_subgrids, int edge, int ghost, int 
         st = fail(OCT_E_NOMEM, "cudaMalloc dt cap");
     if (st == OCT_OK && cudaMemset(h->d_dtcap, 0, sizeof(double)) != cudaSuccess)
         st = fail(OCT_E_CUDA, "cudaMemset dt cap");
+    if (st == OCT_OK && cudaMalloc(&h->d_ticket, 2 * sizeof(int)) != cudaSuccess)
+        st = fail(OCT_E_NOMEM, "cudaMalloc ticket");
+    if (st == OCT_OK && cudaMemset(h->d_ticket, 0, 2 * sizeof(int)) != cudaSuccess)
+        st = fail(OCT_E_CUDA, "cudaMemset ticket");
     if (st != OCT_OK) {
         oct_hydro_destroy(h);
         return st;
@@ -754,9 +829,12 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
     const bool reflux = h->bc == OCT_BC_AMR && h->n_corr_cells > 0;
     A.faces = reflux ? h->d_faces : nullptr;
     A.face_slot = reflux ? h->d_face_slot : nullptr;
+    A.order = h->d_order;
+    A.ticket = h->d_ticket;
     const int form = form_of(h), mode = h->tile_mode;
-    const int per_sm = h->cta_use[form][mode] > 0 ? h->cta_use[form][mode] : h->ctas_per_sm[form][mode];
-    int grid = std::min<int>(A.n_items, h->n_sm * per_sm);
+    if (h->items_mode != mode || h->items_grid != grid_ctas(h))
+        return fail(OCT_E_STATE, "work items were cut for another launch shape");
+    int grid = std::min<int>(A.n_items, grid_ctas(h));
     CUDA_TRY(rhs_launch(form, mode, grid, st, A));
     CUDA_TRY(cudaGetLastError());
     if (reflux) {
@@ -789,6 +867,8 @@ extern "C" oct_status oct_hydro_rhs(oct_hydro_t h, const double *U, double *dUdt
     const char *d0 = (const char *)dUdt, *d1 = d0 + h->rhs_len * 8;
     if (u0 < d1 && d0 < u1)
         return fail(OCT_E_ARG, "U and dUdt overlap");
+    if ((st = sync_items(h)) != OCT_OK)
+        return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if ((st = launch_rhs(h, U, dUdt, s)) != OCT_OK)
         return st;
@@ -819,6 +899,8 @@ extern "C" oct_status oct_hydro_max_dt(oct_hydro_t h, const double *U, double *d
     if (!dt_host_out)
         return fail(OCT_E_ARG, "dt_host_out is NULL");
     if ((st = ensure_scratch(h)) != OCT_OK)
+        return st;
+    if ((st = sync_items(h)) != OCT_OK)
         return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if ((st = launch_rhs(h, U, h->d_L, s)) != OCT_OK)
@@ -916,6 +998,8 @@ extern "C" oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_use
         return st;
     if ((st = ensure_scratch(h)) != OCT_OK)
         return st;
+    if ((st = sync_items(h)) != OCT_OK)
+        return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (h->graphs.size() >= 16 && !h->graphs.count(U))
         drop_graphs(h);  // bound the per-state-pointer graph cache
@@ -988,6 +1072,8 @@ extern "C" oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, do
         CUDA_TRY(cudaMalloc(&h->d_Uhost, sizeof(double) * h->state_len));
     if (!h->d_Lhost)
         CUDA_TRY(cudaMalloc(&h->d_Lhost, sizeof(double) * std::max<long long>(1, h->rhs_len)));
+    if ((st = sync_items(h)) != OCT_OK)
+        return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     CUDA_TRY(cudaMemcpyAsync(h->d_Uhost, U_host, sizeof(double) * h->state_len, cudaMemcpyHostToDevice, s));
     if ((st = launch_rhs(h, h->d_Uhost, h->d_Lhost, s)) != OCT_OK)
@@ -1071,9 +1157,7 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
         if (tune_lookup(key, &mode, &use) && mode < RHS_MODES && use <= h->ctas_per_sm[form_of(h)][mode]) {
             h->tile_mode = mode;
             h->cta_use[form_of(h)][mode] = use;
-            build_items(h);
-            drop_graphs(h);
-            return upload_items(h);
+            return sync_items(h);
         }
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -1089,11 +1173,11 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
         if (h->ctas_per_sm[prec][mode] < 1)
             continue;  // this launch shape does not fit with this field count
         h->tile_mode = mode;
-        build_items(h);
-        if ((st = upload_items(h)) != OCT_OK)
-            return st;
         for (int use = 1; use <= h->ctas_per_sm[prec][mode]; use++) {
             h->cta_use[prec][mode] = use;
+            // the items are cut for this grid
+            if ((st = sync_items(h)) != OCT_OK)
+                return st;
             float tot = 0.0f;
             for (int rep = 0; rep < 3; rep++) {
                 CUDA_TRY(cudaEventRecord(e0, s));
@@ -1119,9 +1203,7 @@ extern "C" oct_status oct_hydro_autotune(oct_hydro_t h, const double *U_sample, 
     h->tile_mode = best_mode;
     h->cta_use[prec][best_mode] = best_use;
     tune_store(key, best_mode, best_use);
-    build_items(h);
-    drop_graphs(h);
-    return upload_items(h);
+    return sync_items(h);
 }
 
 extern "C" oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *ctas_per_sm, int *n_items)
@@ -1167,6 +1249,7 @@ extern "C" void oct_hydro_destroy(oct_hydro_t h)
     dfree(h->d_flags);
     dfree(h->d_dt);
     dfree(h->d_dtcap);
+    dfree(h->d_ticket);
     delete h;
 }
 
@@ -1334,6 +1417,8 @@ extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_s
     A.inv_gm1 = 1.0 / (gamma - 1.0);
     A.faces = nullptr;
     A.face_slot = nullptr;
+    A.order = nullptr;
+    A.ticket = nullptr;
     int grid = std::min(n_items, D->n_sm * D->ctas[precision]);
     CUDA_TRY(rhs_launch(precision, 0, grid, s, A));
     dt_kernel<<<1, 1024, 0, s>>>(n_items, d_items, dx, d_amax, cfl, nullptr, dt);

@@ -98,6 +98,10 @@ OCT_DECLARE(fp64_m2_prim)
 OCT_DECLARE(mixed_m0_prim)
 OCT_DECLARE(mixed_m1_prim)
 OCT_DECLARE(mixed_m2_prim)
+OCT_DECLARE(fp64_m3)
+OCT_DECLARE(mixed_m3)
+OCT_DECLARE(fp64_m3_prim)
+OCT_DECLARE(mixed_m3_prim)
 #undef OCT_DECLARE
 
 namespace {
@@ -105,15 +109,15 @@ using prepare_fn = cudaError_t (*)(int, int *);
 using launch_fn = cudaError_t (*)(int, cudaStream_t, const RhsArgs &);
 // [form][mode]; form = precision + 2 * (primitive reconstruction)
 const prepare_fn k_prepare[4][RHS_MODES] = {
-    {rhs_prepare_fp64_m0, rhs_prepare_fp64_m1, rhs_prepare_fp64_m2},
-    {rhs_prepare_mixed_m0, rhs_prepare_mixed_m1, rhs_prepare_mixed_m2},
-    {rhs_prepare_fp64_m0_prim, rhs_prepare_fp64_m1_prim, rhs_prepare_fp64_m2_prim},
-    {rhs_prepare_mixed_m0_prim, rhs_prepare_mixed_m1_prim, rhs_prepare_mixed_m2_prim}};
+    {rhs_prepare_fp64_m0, rhs_prepare_fp64_m1, rhs_prepare_fp64_m2, rhs_prepare_fp64_m3},
+    {rhs_prepare_mixed_m0, rhs_prepare_mixed_m1, rhs_prepare_mixed_m2, rhs_prepare_mixed_m3},
+    {rhs_prepare_fp64_m0_prim, rhs_prepare_fp64_m1_prim, rhs_prepare_fp64_m2_prim, rhs_prepare_fp64_m3_prim},
+    {rhs_prepare_mixed_m0_prim, rhs_prepare_mixed_m1_prim, rhs_prepare_mixed_m2_prim, rhs_prepare_mixed_m3_prim}};
 const launch_fn k_launch[4][RHS_MODES] = {
-    {rhs_launch_fp64_m0, rhs_launch_fp64_m1, rhs_launch_fp64_m2},
-    {rhs_launch_mixed_m0, rhs_launch_mixed_m1, rhs_launch_mixed_m2},
-    {rhs_launch_fp64_m0_prim, rhs_launch_fp64_m1_prim, rhs_launch_fp64_m2_prim},
-    {rhs_launch_mixed_m0_prim, rhs_launch_mixed_m1_prim, rhs_launch_mixed_m2_prim}};
+    {rhs_launch_fp64_m0, rhs_launch_fp64_m1, rhs_launch_fp64_m2, rhs_launch_fp64_m3},
+    {rhs_launch_mixed_m0, rhs_launch_mixed_m1, rhs_launch_mixed_m2, rhs_launch_mixed_m3},
+    {rhs_launch_fp64_m0_prim, rhs_launch_fp64_m1_prim, rhs_launch_fp64_m2_prim, rhs_launch_fp64_m3_prim},
+    {rhs_launch_mixed_m0_prim, rhs_launch_mixed_m1_prim, rhs_launch_mixed_m2_prim, rhs_launch_mixed_m3_prim}};
 }  // namespace
 
 size_t rhs_smem_bytes(int nf, int form, int mode)

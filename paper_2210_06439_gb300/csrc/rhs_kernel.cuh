@@ -488,7 +488,12 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                 first_g[a] = g;
     bool bad = false;
 
-    for (int it = blockIdx.x; it < A.n_items; it += gridDim.x) {
+    // work items: the first by block index, the rest from the ticket counter
+    // in execution order (largest first), so that CTAs which finish early take
+    // the remaining items; without a ticket, a static round robin
+    __shared__ int s_next;
+    for (int k = blockIdx.x; k < A.n_items;) {
+        const int it = A.order != nullptr ? A.order[k] : k;
         const WorkItem W = A.items[it];
         const int s = W.s, x0 = W.x0, y0 = W.y0, tx = W.txty & 0xFF, ty = (W.txty >> 8) & 0xFF;
         const int E = A.edge[s], B = E + 2 * NG;
@@ -898,8 +903,19 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
             for (int w = 0; w < NT / 32; w++)
                 m = fmax(m, red[w]);
             A.amax_tile[it] = m;
+            s_next = A.ticket != nullptr ? (int)gridDim.x + atomicAdd(A.ticket, 1) : k + (int)gridDim.x;
         }
         __syncthreads();
+        k = s_next;
+    }
+    if (A.ticket != nullptr && tid == 0) {
+        // every CTA has drawn its last ticket before it counts itself done: the
+        // last one to finish returns both counters to zero for the next launch
+        __threadfence();
+        if (atomicAdd(A.ticket + 1, 1) == (int)gridDim.x - 1) {
+            atomicExch(A.ticket, 0);
+            atomicExch(A.ticket + 1, 0);
+        }
     }
     if (bad)
         atomicOr(A.flags, 1u);

@@ -12,8 +12,9 @@ namespace octh {
 // form: precision (0 FP64, 1 mixed) + 2 for primitive reconstruction; mode
 // (the launch shape): 0 tile capacity 8x8 with 256 threads (one CTA per SM),
 // 1 capacity 8x4 with 256 threads (two CTAs per SM for FP64, three for the
-// mixed form), 2 capacity 8x8 with 512 threads (one CTA per SM).
-constexpr int RHS_MODES = 3;
+// mixed form), 2 capacity 8x8 with 512 threads (one CTA per SM), 3 capacity
+// 8x8 with 1024 threads (one CTA per SM, at most 64 registers a thread).
+constexpr int RHS_MODES = 4;
 size_t rhs_smem_bytes(int nf, int form, int mode);
 bool build_group_tables(GroupTab *groups);
 cudaError_t rhs_prepare(int form, int mode, int nf, int *ctas_per_sm);
