@@ -890,7 +890,12 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
             }
             if (kz + 3 <= E + 2)
                 stage_plane(kz + 3);
-            __syncthreads();
+            // the staged plane must be complete before the next phase A reads it;
+            // without staging nothing here is read by the next plane's phase A or
+            // phase B1, and its phase B2 (which rewrites the face sums and the
+            // z-face slot read above) comes after two more barriers
+            if constexpr (STAGED)
+                __syncthreads();
         }
         // ---- max signal speed of this item ----
         for (int o = 16; o > 0; o >>= 1)
