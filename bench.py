@@ -122,7 +122,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
 # DRAM bytes (read + write) of one launch of the FP64 RHS kernel on the
 # periodic 64^3 box, from the ncu capture summarised in
 # profiles/rhs_kernel_fp64_periodic_box_64.md; None once the kernel changes.
-RHS_FP64_TRAFFIC = {"periodic_box_64": 123504128 + 14685440}
+RHS_FP64_TRAFFIC = {"periodic_box_64": 123908096 + 15099392}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
@@ -321,7 +321,7 @@ def run_ours(args, rank, world):
                                    "unit": "TFLOP/s", "frac": mx_tflops / FP32_PEAK_TFLOPS,
                                    "hbm_gbs": mx_gbs, "hbm_frac": mx_gbs / hbm_peak}},
         "roofline": {"bound": "alu", "achieved": rhs_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": rhs_tflops / FP64_PEAK_TFLOPS, "traffic": RHS_FP64_TRAFFIC.get(args.workload),
+                     "frac": rhs_tflops / FP64_PEAK_TFLOPS, "traffic": RHS_FP64_TRAFFIC.get(args.workload) if args.recon == 0 else None,
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "kernel": "rhs_kernel<double> (FP64 RHS)", "ops_per_cell": ops_cell,
                      "peak_source": "nominal FP64 of GB300 (1.25 TFLOP/s); a DFMA loop measured 1.0",

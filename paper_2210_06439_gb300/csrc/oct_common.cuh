@@ -68,64 +68,6 @@ struct RhsArgs {
     int *ticket;
 };
 
-// ---------------------------------------------------------------------------
-// Exact conversions between FP64 and FP32 on the integer pipe.  On this GPU a
-// cvt between the two formats issues on the FP64 pipe (about 1/64 of the FP32
-// rate), so the mixed-precision kernels convert with integer operations
-// instead.  Both follow IEEE 754 binary64 <-> binary32 conversion with
-// round-to-nearest-even, including subnormals, infinities and NaN.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float d2f_rn(double d)
-{
-    unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-    int e = (int)((b >> 52) & 0x7FF);
-    unsigned long long m = b & 0x000FFFFFFFFFFFFFull;
-    int fe = e - 1023 + 127;
-    if (fe > 0 && fe < 255) {
-        // normal result: keep 23 bits, round the 29 dropped ones to even
-        unsigned int keep = (unsigned int)(m >> 29);
-        unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);
-        unsigned int r = ((unsigned int)fe << 23) | keep;
-        r += (rem > 0x10000000u) || (rem == 0x10000000u && (keep & 1u));
-        return __uint_as_float(sign | r);  // a carry into exponent 255 gives inf, as required
-    }
-    if (e == 0x7FF)
-        return __uint_as_float(sign | 0x7F800000u | (m ? 0x00400000u : 0u));
-    if (fe >= 255)
-        return __uint_as_float(sign | 0x7F800000u);
-    // subnormal or zero result
-    if (e == 0 || fe < -24)
-        return __uint_as_float(sign);
-    m |= 0x0010000000000000ull;
-    int sh = 29 + 1 - fe;  // 30..54
-    unsigned long long keep = m >> sh;
-    unsigned long long rem = m & ((1ull << sh) - 1);
-    unsigned long long half = 1ull << (sh - 1);
-    keep += (rem > half) || (rem == half && (keep & 1ull));
-    return __uint_as_float(sign | (unsigned int)keep);
-}
-
-__device__ __forceinline__ double f2d(float f)
-{
-    unsigned int b = __float_as_uint(f);
-    unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
-    unsigned int e = (b >> 23) & 0xFFu;
-    unsigned long long m = b & 0x7FFFFFu;
-    if (e != 0 && e != 0xFF)
-        return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | (m << 29)));
-    if (e == 0xFF)
-        return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | (m << 29)));
-    if (m == 0)
-        return __longlong_as_double((long long)sign);
-    // subnormal float: normalise
-    int lz = __clz((int)(m << 9));  // leading zeros within the 23-bit field
-    m <<= (lz + 1);
-    m &= 0x7FFFFFu;
-    int ee = 1 - 127 - (lz + 1) + 1023;
-    return __longlong_as_double((long long)(sign | ((unsigned long long)ee << 52) | (m << 29)));
-}
-
 // FP32-estimate helpers shared by the kernels (FP64 arithmetic on this GPU
 // runs at about 1/64 of the FP32 rate).
 __device__ __forceinline__ long long dbits_c(double x) { return __double_as_longlong(x); }

@@ -1,8 +1,9 @@
 // rhs_instance.cuh -- host entry points of one RHS kernel instance.  Each
-// instance (FP64 or mixed form, launch shape -- 8x8 tiles with 256 or 512
-// threads, 8x4 tiles with 256 --, conserved or primitive reconstruction) is compiled in a translation unit of its own so
-// that the instances build in parallel; each unit uploads its own copy of the
-// line-group tables into its constant memory.
+// instance (FP64 or mixed form; launch shape: 8x8 tiles with 256, 512 or 1024
+// threads, or 8x4 tiles with 256; conserved or primitive reconstruction) is
+// compiled in a translation unit of its own so that the instances build in
+// parallel; each unit uploads its own copy of the line-group tables into its
+// constant memory.
 #pragma once
 #include "rhs_kernel.cuh"
 #include "rhs_launch.h"

@@ -9,8 +9,10 @@
 // Newton-Cotes (tensor Simpson) points of every face with a local speed per
 // point, the face average, and the finite-volume divergence.
 //
-// GPU organisation.  A CTA owns one work item: a tx * ty column of a subgrid
-// (tx, ty <= 8) and streams through its z planes kz = -1 .. E.  For each plane
+// GPU organisation.  A persistent CTA takes work items one after another (the
+// first by block index, the rest from a device counter); an item is a tx * ty
+// column of a subgrid (tx, ty <= 8), and the CTA streams through its z planes
+// kz = -1 .. E.  For each plane
 // the 13 lines are processed in 4 groups (the axis lines x, y, z; the xy and
 // xz diagonals; the yz diagonals; the body diagonals); within a group both sides of each
 // face quadrature point are available, so the flux of that point is formed as
@@ -43,9 +45,12 @@ template <> struct Num<double> {
     __device__ static __forceinline__ double to_d(double x) { return x; }
     __device__ static __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 };
+// The mixed form converts with the hardware cvt (exact, round to nearest
+// even): it issues on the FP64 pipe, which this form leaves idle, in one issue
+// slot where a conversion in integer code takes about fifteen.
 template <> struct Num<float> {
-    __device__ static __forceinline__ float from_d(double x) { return d2f_rn(x); }
-    __device__ static __forceinline__ double to_d(float x) { return f2d(x); }
+    __device__ static __forceinline__ float from_d(double x) { return __double2float_rn(x); }
+    __device__ static __forceinline__ double to_d(float x) { return (double)x; }
     __device__ static __forceinline__ float pow_(float x, float y) { return powf(x, y); }
 };
 
@@ -519,7 +524,7 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                     int f = q / (rows * cols), r = q - f * (rows * cols);
                     int jj = r / cols, ii = r - jj * cols;
                     double v = __ldg(Ub + f * FS + (long long)(kz + NG) * B * B + (long long)(y0 + jj) * B + (x0 + ii));
-                    raw[((slot * nf + f) * RWY + jj) * RWX + ii] = d2f_rn(v);
+                    raw[((slot * nf + f) * RWY + jj) * RWX + ii] = __double2float_rn(v);
                 }
             }
         };
