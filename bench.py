@@ -122,7 +122,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
 # DRAM bytes (read + write) of one launch of the FP64 RHS kernel on the
 # periodic 64^3 box, from the ncu capture summarised in
 # profiles/rhs_kernel_fp64_periodic_box_64.md; None once the kernel changes.
-RHS_FP64_TRAFFIC = {"periodic_box_64": 123908096 + 15099392}
+RHS_FP64_TRAFFIC = {"periodic_box_64": 123444992 + 14765056}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
