@@ -319,6 +319,13 @@ __device__ __forceinline__ float sound_from_w(float rho, float p, float gamma, b
     return c;
 }
 
+// q / d for the small divisors of a tile (widths, cell counts; 2 <= d < 2^12)
+// as a multiply-high by m = ceil(2^32 / d): exact for q < 2^16, since the
+// rounding error of m adds less than q d / 2^32 < 1/d to q / d.  A plain
+// 32-bit division costs about twenty integer instructions.
+__device__ __forceinline__ unsigned rcp_div(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
+__device__ __forceinline__ int div_by(int q, unsigned m) { return (int)__umulhi((unsigned)q, m); }
+
 // Shared-memory plan of one CTA (dynamic shared memory) for a tile capacity
 // of txm x tym cells and nf fields.
 struct SmemPlan {
@@ -518,6 +525,9 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
         const double *Ub = A.U + A.off[s];
         double *dUb = A.dUdt + A.doff[s];
         const double rdx = 1.0 / A.dx[s];
+        const unsigned m_tx = rcp_div(tx), m_tx1 = rcp_div(tx + 1), m_ty = rcp_div(ty);
+        const int rows_s = ty + 2 * NG, cols_s = tx + 2 * NG;  // staged plane of this item
+        const unsigned m_rc = rcp_div(rows_s * cols_s), m_cols = rcp_div(cols_s);
         const int ncin = tx * ty;
         double amax = 0.0;
         // this subgrid's boundary face fluxes, if wanted (looked up where used:
@@ -530,11 +540,10 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
         auto stage_plane = [&](int kz) {
             if constexpr (STAGED) {
                 int slot = (kz + 3) % 5;
-                int rows = ty + 2 * NG, cols = tx + 2 * NG;
-                int n = nf * rows * cols;
+                int n = nf * rows_s * cols_s;
                 for (int q = tid; q < n; q += NT) {
-                    int f = q / (rows * cols), r = q - f * (rows * cols);
-                    int jj = r / cols, ii = r - jj * cols;
+                    int f = div_by(q, m_rc), r = q - f * (rows_s * cols_s);
+                    int jj = div_by(r, m_cols), ii = r - jj * cols_s;
                     double v = __ldg(Ub + f * FS + (long long)(kz + NG) * B * B + (long long)(y0 + jj) * B + (x0 + ii));
                     raw[((slot * nf + f) * RWY + jj) * RWX + ii] = __double2float_rn(v);
                 }
@@ -553,18 +562,18 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                 continue;
             int i, j;
             if (c < ncin) {
-                i = c % tx;
-                j = c / tx;
+                j = div_by(c, m_tx);
+                i = c - j * tx;
             } else {
                 int r = c - ncin;
                 if ((t & 1) && r < 2 * ty) {
                     i = (r < ty) ? -1 : tx;
-                    j = r % ty;
+                    j = r - div_by(r, m_ty) * ty;
                 } else {
                     if (t & 1)
                         r -= 2 * ty;
                     j = (r < tx) ? -1 : ty;
-                    i = r % tx;
+                    i = r - div_by(r, m_tx) * tx;
                 }
             }
             lists[q] = (i + 1) | ((j + 1) << 8) | (cidx(i, j, tx, ty) << 16);
@@ -572,7 +581,7 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
         unsigned magic[4];
 #pragma unroll
         for (int t = 0; t < 4; t++)
-            magic[t] = (unsigned)((0x100000000ULL + nlist[t] - 1) / nlist[t]);
+            magic[t] = rcp_div(nlist[t]);
 
         for (int kz = -3; kz <= 1; kz++)
             stage_plane(kz);
@@ -711,14 +720,14 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                     const bool act = tid < nfx + nfy + nfz;
                     if (tid < nfx) {
                         axis = 0;
-                        int p = tid % (tx + 1), j = tid / (tx + 1);
+                        int j = div_by(tid, m_tx1), p = tid - j * (tx + 1);
                         cl = cidx(p - 1, j, tx, ty);
                         cr = cidx(p, j, tx, ty);
                         fslot = tid;
                     } else if (tid < nfx + nfy) {
                         axis = 1;
                         int r = tid - nfx;
-                        int i = r % tx, p = r / tx;
+                        int p = div_by(r, m_tx), i = r - p * tx;
                         cl = cidx(i, p - 1, tx, ty);
                         cr = cidx(i, p, tx, ty);
                         fslot = r;
@@ -850,8 +859,8 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
             // thread for each (field, cell), so dxy is read before it is
             // rewritten; then the next plane is staged ----
             for (int q = tid; q < nf * ncin; q += NT) {
-                int f = q / ncin, c = q - f * ncin;
-                int i = c % tx, j = c / tx;
+                int f = div_by(q, magic[0]), c = q - f * ncin;
+                int j = div_by(c, m_tx), i = c - j * tx;
                 if (kz >= 1) {
                     const T *zp = zacc + (kz & 1) * nf * C64;
                     const T *zm = zacc + ((kz - 1) & 1) * nf * C64;
@@ -874,8 +883,8 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                     const T *zs = zacc + ((kz == 1 ? kz - 1 : kz) & 1) * nf * C64;
                     double *o = fb + (long long)(kz == 1 ? 4 : 5) * nf * E * E;
                     for (int q = tid; q < nf * ncin; q += NT) {
-                        int f = q / ncin, c = q - f * ncin;
-                        int i = c % tx, j = c / tx;
+                        int f = div_by(q, magic[0]), c = q - f * ncin;
+                        int j = div_by(c, m_tx), i = c - j * tx;
                         o[(long long)f * E * E + (y0 + j) * E + (x0 + i)] = Num<T>::to_d(zs[f * C64 + c]);
                     }
                 }
@@ -885,7 +894,7 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                     const long long EE = (long long)E * E;
                     if (x0 == 0 || x0 + tx == E)
                         for (int q = tid; q < nf * ty; q += NT) {
-                            int f = q / ty, j = q - f * ty;
+                            int f = div_by(q, m_ty), j = q - f * ty;
                             const T *fx = faccx + f * FXS + j * (tx + 1);
                             const long long o = f * EE + (long long)kz * E + (y0 + j);
                             if (x0 == 0)
@@ -895,7 +904,7 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                         }
                     if (y0 == 0 || y0 + ty == E)
                         for (int q = tid; q < nf * tx; q += NT) {
-                            int f = q / tx, i = q - f * tx;
+                            int f = div_by(q, m_tx), i = q - f * tx;
                             const T *fy = faccy + f * FYS;
                             const long long o = f * EE + (long long)kz * E + (x0 + i);
                             if (y0 == 0)
