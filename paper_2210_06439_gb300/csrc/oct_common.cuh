@@ -68,6 +68,14 @@ struct RhsArgs {
     int *ticket;
 };
 
+// q / d for the small divisors of the kernels' index arithmetic (tile widths,
+// edges, cell and ghost-cell counts; 2 <= d < 2^12) as a multiply-high by
+// m = ceil(2^32 / d): exact for q < 2^16, since the rounding error of m adds
+// less than q d / 2^32 < 1/d to q / d.  A plain 32-bit division costs about
+// twenty integer instructions.
+__device__ __forceinline__ unsigned rcp_div(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
+__device__ __forceinline__ int div_by(int q, unsigned m) { return (int)__umulhi((unsigned)q, m); }
+
 // FP32-estimate helpers shared by the kernels (FP64 arithmetic on this GPU
 // runs at about 1/64 of the FP32 rate).
 __device__ __forceinline__ long long dbits_c(double x) { return __double_as_longlong(x); }

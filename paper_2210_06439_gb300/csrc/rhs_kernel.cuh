@@ -319,13 +319,6 @@ __device__ __forceinline__ float sound_from_w(float rho, float p, float gamma, b
     return c;
 }
 
-// q / d for the small divisors of a tile (widths, cell counts; 2 <= d < 2^12)
-// as a multiply-high by m = ceil(2^32 / d): exact for q < 2^16, since the
-// rounding error of m adds less than q d / 2^32 < 1/d to q / d.  A plain
-// 32-bit division costs about twenty integer instructions.
-__device__ __forceinline__ unsigned rcp_div(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
-__device__ __forceinline__ int div_by(int q, unsigned m) { return (int)__umulhi((unsigned)q, m); }
-
 // Shared-memory plan of one CTA (dynamic shared memory) for a tile capacity
 // of txm x tym cells and nf fields.
 struct SmemPlan {

@@ -119,7 +119,9 @@ __global__ void combine_kernel(CombineArgs A, int n_sub, const long long *cell_b
         a = 1.0 / 3.0;
         b = 2.0 / 3.0;
     }
-    const int x = c % E, y = (c / E) % E, z = c / (E * E);
+    const unsigned m_E = E == 8 ? rcp_div(8) : (E == 12 ? rcp_div(12) : rcp_div(16));
+    const int zy = div_by(c, m_E), z = div_by(zy, m_E);
+    const int x = c - zy * E, y = zy - z * E;
     const long long gi = A.off[s] + ((long long)(z + NG) * B + (y + NG)) * B + (x + NG);
     const long long li = A.doff[s] + c;
     double xv[MAXNF], lv[MAXNF], u0[MAXNF];
@@ -167,6 +169,44 @@ __global__ void combine_kernel(CombineArgs A, int n_sub, const long long *cell_b
         atomicOr(A.flags, 2u);
 }
 
+// The ghost shell of a subgrid of edge E, enumerated as: the two z slabs
+// (3 planes of B x B each, lower first), then the two y slabs within the
+// interior z range (3 rows of B each per plane), then the two x slabs within
+// the interior y and z ranges (3 columns each); coords(q) gives entry q's
+// position (x, y, z), relative to the interior origin.
+struct GhostShell {
+    int E, B, nzs, nys, nxs, total;
+    unsigned m_B, m_E, m_nzs, m_nys, m_nxs;  // reciprocals for div_by
+    __device__ explicit GhostShell(int e)
+        : E(e), B(e + 2 * NG), nzs(NG * B * B), nys(NG * B * e), nxs(NG * e * e),
+          total(2 * nzs + 2 * nys + 2 * nxs), m_B(rcp_div(B)), m_E(rcp_div(e)), m_nzs(rcp_div(nzs)),
+          m_nys(rcp_div(nys)), m_nxs(rcp_div(nxs))
+    {
+    }
+    __device__ void coords(int q, int g[3]) const
+    {
+        if (q < 2 * nzs) {
+            const int side = div_by(q, m_nzs), r = q - side * nzs;
+            const int a = div_by(r, m_B), b = div_by(a, m_B);
+            g[0] = r - a * B - NG;
+            g[1] = a - b * B - NG;
+            g[2] = b + (side ? E : -NG);
+        } else if (q < 2 * nzs + 2 * nys) {
+            const int r0 = q - 2 * nzs, side = div_by(r0, m_nys), r = r0 - side * nys;
+            const int a = div_by(r, m_B);
+            g[0] = r - a * B - NG;
+            g[1] = a % NG + (side ? E : -NG);
+            g[2] = a / NG;
+        } else {
+            const int r0 = q - 2 * nzs - 2 * nys, side = div_by(r0, m_nxs), r = r0 - side * nxs;
+            const int a = r / NG, b = div_by(a, m_E);
+            g[0] = r - a * NG + (side ? E : -NG);
+            g[1] = a - b * E;
+            g[2] = b;
+        }
+    }
+};
+
 __device__ __forceinline__ int nb_slot(int dx, int dy, int dz)
 {
     int n = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
@@ -186,29 +226,11 @@ __global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf
     const int B = E + 2 * NG;
     const long long FS = (long long)B * B * B;
     const int *nb = nbr + 26 * (long long)s;
-    const int nzs = NG * B * B;   // cells of one z slab (3 planes)
-    const int nys = NG * B * E;   // one y slab within the interior z range
-    const int nxs = NG * E * E;   // one x slab within the interior y and z range
-    const int total = 2 * nzs + 2 * nys + 2 * nxs;
+    const GhostShell sh(E);
     bool err = false;
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    for (int q = threadIdx.x; q < sh.total; q += blockDim.x) {
         int g[3];
-        if (q < 2 * nzs) {
-            const int r = q % nzs, side = q / nzs;
-            g[0] = r % B - NG;
-            g[1] = (r / B) % B - NG;
-            g[2] = r / (B * B) + (side ? E : -NG);
-        } else if (q < 2 * nzs + 2 * nys) {
-            const int r0 = q - 2 * nzs, r = r0 % nys, side = r0 / nys;
-            g[0] = r % B - NG;
-            g[1] = (r / B) % NG + (side ? E : -NG);
-            g[2] = r / (B * NG);
-        } else {
-            const int r0 = q - 2 * nzs - 2 * nys, r = r0 % nxs, side = r0 / nxs;
-            g[0] = r % NG + (side ? E : -NG);
-            g[1] = (r / NG) % E;
-            g[2] = r / (NG * E);
-        }
+        sh.coords(q, g);
         const long long di = off[s] + ((long long)(g[2] + NG) * B + (g[1] + NG)) * B + (g[0] + NG);
         int d[3];
 #pragma unroll
@@ -263,31 +285,15 @@ __global__ void amr_ghost_kernel(double *U, int E, const long long *off, int nf,
     const int s = blockIdx.x;
     const int B = E + 2 * NG;
     const long long FS = (long long)B * B * B;
-    const int nzs = NG * B * B, nys = NG * B * E, nxs = NG * E * E;
-    const int total = 2 * nzs + 2 * nys + 2 * nxs;
-    const int2 *pl = plan + (long long)s * total;
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    const GhostShell sh(E);
+    const int2 *pl = plan + (long long)s * sh.total;
+    for (int q = threadIdx.x; q < sh.total; q += blockDim.x) {
         const int2 e = pl[q];
         const bool prolong = (e.x & 0x40000000) && e.x >= 0;
         if (prolong != (pass == 1))
             continue;
         int g[3];
-        if (q < 2 * nzs) {
-            const int r = q % nzs, side = q / nzs;
-            g[0] = r % B - NG;
-            g[1] = (r / B) % B - NG;
-            g[2] = r / (B * B) + (side ? E : -NG);
-        } else if (q < 2 * nzs + 2 * nys) {
-            const int r0 = q - 2 * nzs, r = r0 % nys, side = r0 / nys;
-            g[0] = r % B - NG;
-            g[1] = (r / B) % NG + (side ? E : -NG);
-            g[2] = r / (B * NG);
-        } else {
-            const int r0 = q - 2 * nzs - 2 * nys, r = r0 % nxs, side = r0 / nxs;
-            g[0] = r % NG + (side ? E : -NG);
-            g[1] = (r / NG) % E;
-            g[2] = r / (NG * E);
-        }
+        sh.coords(q, g);
         const long long di = off[s] + ((long long)(g[2] + NG) * B + (g[1] + NG)) * B + (g[0] + NG);
         const int t = e.x & 0x3FFFFFFF;
         double v[MAXNF];
