@@ -120,9 +120,10 @@ def _peaks():
 
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
 # DRAM bytes (read + write) of one launch of the FP64 RHS kernel on the
-# periodic 64^3 box, from the ncu capture summarised in
-# profiles/rhs_kernel_fp64_periodic_box_64.md; None once the kernel changes.
-RHS_FP64_TRAFFIC = {"periodic_box_64": 123444992 + 14765056}
+# periodic 64^3 box (8x8 tiles, 1024 threads), from an ncu capture of that
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel
+# changes.
+RHS_FP64_TRAFFIC = {"periodic_box_64": 123485440 + 15046400}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
