@@ -43,7 +43,6 @@ template <class T> struct Num;
 template <> struct Num<double> {
     __device__ static __forceinline__ double from_d(double x) { return x; }
     __device__ static __forceinline__ double to_d(double x) { return x; }
-    __device__ static __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 };
 // The mixed form converts with the hardware cvt (exact, round to nearest
 // even): it issues on the FP64 pipe, which this form leaves idle, in one issue
@@ -51,7 +50,6 @@ template <> struct Num<double> {
 template <> struct Num<float> {
     __device__ static __forceinline__ float from_d(double x) { return __double2float_rn(x); }
     __device__ static __forceinline__ double to_d(float x) { return (double)x; }
-    __device__ static __forceinline__ float pow_(float x, float y) { return powf(x, y); }
 };
 
 // ---------------------------------------------------------------------------
@@ -63,12 +61,6 @@ template <> struct Num<float> {
 // path), and reciprocals and square roots start from an FP32 estimate and
 // are refined by Newton-Raphson steps in FP64.
 // ---------------------------------------------------------------------------
-constexpr long long ABSM = 0x7FFFFFFFFFFFFFFFLL;
-constexpr long long SGNM = (long long)0x8000000000000000ULL;
-constexpr long long EXP1 = 1LL << 52;
-
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
-__device__ __forceinline__ double bitsd(long long b) { return __longlong_as_double(b); }
 
 // sqrt(q): FP32 reciprocal-square-root estimate y (about 2^-22), s = q y,
 // then two Newton (Heron) corrections s <- s + (q - s^2) y / 2.
