@@ -84,3 +84,38 @@ def test_every_launch_shape_matches_oracle(tmp_path, monkeypatch, precision):
                 np.testing.assert_allclose(am.cpu().numpy(), am_o, rtol=1e-12 if precision == 0 else 1e-5)
         assert {(0, 1), (1, 1), (2, 1), (3, 1)} <= seen, seen
         H.close()
+
+
+def test_work_items_cut_the_last_round(tmp_path, monkeypatch):
+    """The work list of each launch shape: one item per tile; when the tiles
+    are all of one size and the leftover r = tiles mod G of the last round of
+    a G-CTA persistent grid is at most G/2, those r tiles are cut in half
+    (r more items); mixed subgrid edges are never cut."""
+    import torch
+    from paper_2210_06439_gb300 import binding
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("OCT_HYDRO_TUNE_CACHE", str(path))
+
+    def expected(tiles, G, uniform):
+        r = tiles % G
+        return tiles + r if (uniform and r > 0 and 2 * r <= G) else tiles
+
+    cases = [(oracle_filled(inputs.periodic_box()), {0: 512, 1: 1024, 2: 512, 3: 512}, True),
+             (oracle_filled(inputs.periodic_box(nsub=2)), {0: 8, 1: 16, 2: 8, 3: 8}, True),
+             (inputs.mixed_levels(n=30), {0: 90, 1: 160, 2: 90, 3: 90}, False)]
+    for p, tiles, uniform in cases:
+        U = torch.from_numpy(p.U).cuda()
+        H = binding.Hydro.from_problem(p, precision=0)
+        path.write_text("")
+        H.autotune(U)
+        key = path.read_text().split()[0]
+        for mode in range(4):
+            for use in (1, 2):
+                path.write_text(f"{key} {mode} {use}\n")
+                H.autotune(U)
+                m, u, n = H.launch_info()
+                if (m, u) != (mode, use):
+                    continue
+                assert n == expected(tiles[mode], n_sm * use, uniform), (p.name, mode, use, n)
+        H.close()
