@@ -88,7 +88,10 @@ __device__ __forceinline__ double tau_of_eint(double e, double gamma)
 // then the floors rho >= rho_floor, rho_i >= 0, the tau re-synchronisation
 // tau = e_int^(1/gamma) where e_int = E - |s|^2/(2 rho) > eps2 E, and tau >= 0.
 // All loads of a cell are issued before its stores.
-__global__ void combine_kernel(CombineArgs A, int n_sub, const long long *cell_begin, long long n_cells)
+// Three CTAs per SM (80 registers): the kernel waits on memory, and 24 warps
+// per SM hide more of it than the 16 that 103 registers allowed.
+__global__ void __launch_bounds__(256, 3)
+    combine_kernel(CombineArgs A, int n_sub, const long long *cell_begin, long long n_cells)
 {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n_cells)
