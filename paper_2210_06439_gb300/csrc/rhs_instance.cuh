@@ -18,9 +18,13 @@
         cudaError_t t = cudaMemcpyToSymbol(c_groups, gs, sizeof gs);                                          \
         if (t != cudaSuccess)                                                                                 \
             return t;                                                                                         \
+        /* the attribute is process-wide: it is set to the plan of the largest field                       \
+           count, never lowered, so that handles of any field count (and the                                \
+           allocation-free call) launch under it; the occupancy follows this nf */                          \
         const size_t sm = smem_plan(nf, sizeof(T), STAGED, TXM, TYM).total;                                   \
+        const size_t sm_max = smem_plan(MAXNF, sizeof(T), STAGED, TXM, TYM).total;                            \
         cudaError_t e = cudaFuncSetAttribute(rhs_kernel<T, STAGED, TXM, TYM, MINB, PRIM, NT>,                     \
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);           \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_max);       \
         if (e != cudaSuccess)                                                                                 \
             return e;                                                                                         \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm,                                     \
