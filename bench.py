@@ -3,17 +3,23 @@
 
 One step = one full SSP-RK3 step (three RHS evaluations, the CFL dt
 reduction, three combines with floors and dual-energy re-synchronisation,
-three ghost fills) over the periodic 64^3 box of 512 subgrids of 8^3 cells
-with 5 species, in FP64, replayed from the library's CUDA graph.  Inputs are
-resident in HBM before the timed region; L2 is flushed (256 MiB write)
-between timed steps, each step timed by its own CUDA events on the launching
-stream.  The mixed form and the RHS alone are measured the same way and
-reported beside the headline.
+three ghost fills) over the 256^3 binary-star box (32768 subgrids of 8^3
+cells, 3 ghost layers, 5 species, outflow edges), in FP64, replayed from the
+library's CUDA graph.  Inputs are resident in HBM before the timed region
+(the 7.9 GB state is larger than L2, and L2 is flushed by a 256 MiB write
+before each timed step as well), each step timed by its own CUDA events on
+the launching stream.  The mixed form and the RHS alone are measured the
+same way and reported beside the headline; the FP64 and FP32 FMA peaks the
+roofline divides by are measured in the same process.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME]
+  python bench.py --profile-rhs [--workload NAME] [--precision 0|1] [--reps R]
 
---impl reference times the FP64 CPU oracle (the reference arm of this
-build) on the host cores for the same metric.
+--impl reference times the FP64 CPU oracle (the reference arm) on the host
+cores for the same metric.  --profile-rhs only runs R RHS launches of one
+form on the workload (after one autotuning pass unless --no-autotune), for
+captures under a profiler; it prints no benchmark line.
 """
 from __future__ import annotations
 
@@ -51,6 +57,15 @@ WORKLOADS = {
                    "cells are refined into 64 level-1 subgrids; ghost fill across levels and flux correction at "
                    "coarse-fine faces; the periodic_box law, 5 species, seed 1006",
                    lambda inp: inp.amr_box(n_coarse=8), lambda inp: inp.amr_box(n_coarse=4)),
+}
+# per workload: (edges of its subgrids, species) -- the shape without the data
+SHAPES = {
+    "periodic_box_64": (lambda: [8] * 512, 5),
+    "mixed_levels": (lambda: [(8, 12, 16)[i % 3] for i in range(4096)], 5),
+    "binary_star_128": (lambda: [8] * 4096, 5),
+    "binary_star_256": (lambda: [8] * 32768, 5),
+    "sedov_64": (lambda: [8] * 512, 1),
+    "amr_box_64": (lambda: [8] * 568, 5),
 }
 UNIT = "cell-updates/s"
 STEP = "one step = one SSP-RK3 step (3 RHS + dt + 3 combine/floor + 3 ghost fill), FP64"
@@ -118,13 +133,85 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
-# DRAM bytes (read + write) of one launch of the FP64 RHS kernel on the
-# periodic 64^3 box (8x8 tiles, 1024 threads), from an ncu capture of that
-# kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel
-# changes.
-RHS_FP64_TRAFFIC = {"periodic_box_64": 123485440 + 15046400}
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+# DRAM bytes (read + write) of one launch of the FP64 RHS kernel per
+# workload, from an ncu capture of that kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum) with the kernel as it is now; a workload without an
+# entry reports null.
+RHS_FP64_TRAFFIC = {}
+
+# The 13 PPM lines (canonical directions).
+LINES = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1), (0, 1, -1),
+         (1, 1, 1), (1, -1, -1), (1, -1, 1), (1, 1, -1)]
+
+
+def constant_stencils(U, prob):
+    """(PPM line evaluations counted by rhs_counts, how many of them have a
+    5-cell stencil of one value) over one RHS of the state U (a CUDA tensor
+    in the ghosted layout; uniform edge only, else None).  The FP64 kernel
+    returns such a stencil's own value without any slope arithmetic, so the
+    work it does on a state with uniform regions (the binary star's
+    atmosphere, the Sedov ambient gas) is the method's count minus these.
+    Counted cells as in rhs_counts: all 13 lines of every interior cell, the
+    9 lines with a step across a face for each cell just outside it."""
+    import torch
+    if len(set(int(e) for e in prob.edge)) != 1:
+        return None
+    E, n, nf = int(prob.edge[0]), prob.n_sub, prob.nf
+    B = E + 6
+    stride = int(prob.off[1] - prob.off[0]) if n > 1 else nf * B ** 3
+    if any(int(prob.off[s]) != s * stride for s in (0, n - 1)):
+        return None
+    V = U[: n * stride].view(n, stride)[:, : nf * B ** 3].view(n, nf, B, B, B)
+    R = E + 2  # cells -1 .. E per axis
+    r = torch.arange(R, device=U.device)
+    inner = (r >= 1) & (r <= E)
+    ring = ~inner
+    total = nconst = 0
+    for d in LINES:
+        dx, dy, dz = d
+        m = inner[:, None, None] & inner[None, :, None] & inner[None, None, :]
+        if dx:
+            m = m | (inner[:, None, None] & inner[None, :, None] & ring[None, None, :])
+        if dy:
+            m = m | (inner[:, None, None] & ring[None, :, None] & inner[None, None, :])
+        if dz:
+            m = m | (ring[:, None, None] & inner[None, :, None] & inner[None, None, :])
+        total += int(m.sum().item()) * n * nf
+        for f in range(nf):
+            X = V[:, f]
+            c0 = X[:, 2:2 + R, 2:2 + R, 2:2 + R]
+            const = None
+            for k in (-2, -1, 1, 2):
+                sl = X[:, 2 + k * dz:2 + k * dz + R, 2 + k * dy:2 + k * dy + R, 2 + k * dx:2 + k * dx + R]
+                eq = sl == c0
+                const = eq if const is None else const & eq
+            nconst += int((const & m).sum().item())
+    return total, nconst
+
+
+def bound_of(alu_frac, hbm_frac):
+    """The roof a kernel is closest to, or issue/latency when it is far below
+    both (under half of each)."""
+    if max(alu_frac, hbm_frac) < 0.5:
+        return "issue/latency"
+    return "alu" if alu_frac >= hbm_frac else "hbm"
+
+
+def make_config(args, world):
+    """The benchmark line's config: the workload and its shape (the same for
+    both arms)."""
+    import numpy as np
+    from paper_2210_06439_gb300 import inputs
+    edges_fn, ns = SHAPES[args.workload]
+    edge = np.array(edges_fn(), np.int32)
+    _, state_len = inputs.layout_offsets(edge, 6 + ns)
+    state_bytes = 8 * state_len
+    return {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; {STEP}"
+                        + ("; primitive reconstruction" if args.recon else ""), "subgrids": int(edge.size),
+            "edges": sorted(set(int(e) for e in edge)), "ghost": 3, "n_species": ns,
+            "interior_cells": int(np.sum(edge.astype(np.int64) ** 3)), "parallelism": f"replicas x{world}",
+            "l2": (f"inputs larger than L2 ({state_bytes / 1e9:.2f} GB state); " if state_bytes > 129e6 else "")
+                  + "flushed (256 MiB write) before each timed step"}
 
 
 def reduce_max(v: float, world: int, device="cuda") -> float:
@@ -285,13 +372,25 @@ def run_ours(args, rank, world):
     mixed_err = None
     if args.cpu_baseline and rank == 0 and prob.n_cells <= 2 ** 21:
         mixed_err = mixed_error_table(prob, results, stream)
+    # the FP64 RHS was timed on U0: the stencils its kernel skips there
+    cst = constant_stencils(s64["U0"], prob) if rank == 0 else None
+    # measured FMA peaks of this GPU (one launch of >= 200 ms each, as long as
+    # the FP64 RHS launch of the largest workloads)
+    with torch.cuda.stream(stream):
+        f64_peak, f32_peak = binding.pipe_peaks(200.0, stream=stream)
+    torch.cuda.synchronize()
     if rank != 0:
         return None
     K = args.steps
+    config = make_config(args, world)
+    assert config["interior_cells"] == n_cells and config["subgrids"] == prob.n_sub
     value, ms_step = aggregate(n_cells, world, tot64, K)
     ops_cell, bytes_cell = problem_counts(prob)
+    ops_eff = ops_cell
+    if cst is not None:
+        ops_eff = ops_cell - cst[1] * OPS_PPM / n_cells
     hbm_peak, hbm_src = _peaks()
-    rhs_tflops = ops_cell * n_cells / (rhs64 * 1e-3) / 1e12
+    rhs_tflops = ops_eff * n_cells / (rhs64 * 1e-3) / 1e12
     rhs_gbs = bytes_cell * n_cells / (rhs64 * 1e-3) / 1e9
     mx_tflops = ops_cell * n_cells / (rhsmx * 1e-3) / 1e12
     mx_gbs = bytes_cell * n_cells / (rhsmx * 1e-3) / 1e9
@@ -309,23 +408,26 @@ def run_ours(args, rank, world):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded generators of paper_2210_06439_gb300.inputs)",
-        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; {STEP}"
-                               + ("; primitive reconstruction" if args.recon else ""), "subgrids": prob.n_sub,
-                   "edges": sorted(set(int(e) for e in prob.edge)), "ghost": 3, "n_species": prob.n_species,
-                   "interior_cells": n_cells, "parallelism": f"replicas x{world}",
-                   "l2": "flushed (256 MiB write) before each timed step"},
+        "config": config,
         "rhs": {"value": world * n_cells / (rhs64 * 1e-3), "unit": "RHS cell-updates/s", "ms": rhs64},
         "mixed": {"value": world * n_cells / (totmx / K * 1e-3), "unit": UNIT, "ms_per_step": totmx / K,
                   "rhs_value": world * n_cells / (rhsmx * 1e-3), "rhs_ms": rhsmx,
                   "speedup_vs_fp64_step": ms_step / (totmx / K), "speedup_vs_fp64_rhs": rhs64 / rhsmx,
-                  "rhs_roofline": {"bound": "alu", "achieved": mx_tflops, "peak": FP32_PEAK_TFLOPS,
-                                   "unit": "TFLOP/s", "frac": mx_tflops / FP32_PEAK_TFLOPS,
+                  "rhs_roofline": {"bound": bound_of(mx_tflops / f32_peak, mx_gbs / hbm_peak),
+                                   "achieved": mx_tflops, "peak": f32_peak, "unit": "TFLOP/s",
+                                   "frac": mx_tflops / f32_peak, "peak_source": "measured (FFMA loop, this process)",
                                    "hbm_gbs": mx_gbs, "hbm_frac": mx_gbs / hbm_peak}},
-        "roofline": {"bound": "alu", "achieved": rhs_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": rhs_tflops / FP64_PEAK_TFLOPS, "traffic": RHS_FP64_TRAFFIC.get(args.workload) if args.recon == 0 else None,
+        "roofline": {"bound": "alu", "achieved": rhs_tflops, "peak": f64_peak, "unit": "TFLOP/s",
+                     "frac": rhs_tflops / f64_peak,
+                     "traffic": RHS_FP64_TRAFFIC.get(args.workload) if args.recon == 0 else None,
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "kernel": "rhs_kernel<double> (FP64 RHS)", "ops_per_cell": ops_cell,
-                     "peak_source": "nominal FP64 of GB300 (1.25 TFLOP/s); a DFMA loop measured 1.0",
+                     "kernel": "rhs_kernel<double> (FP64 RHS)",
+                     "ops_per_cell": ops_eff, "method_ops_per_cell": ops_cell,
+                     "ops_note": "FP64 flops of the method's formulas per interior cell, less the PPM lines whose "
+                                 "5-cell stencil holds one value (the kernel returns that value without slope "
+                                 "arithmetic)" + (f": {cst[1]} of {cst[0]} line evaluations" if cst else ""),
+                     "peak_source": "measured (DFMA loop, this process)",
+                     "fp64_peak_tflops": f64_peak, "fp32_peak_tflops": f32_peak,
                      "hbm": {"achieved": rhs_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": rhs_gbs / hbm_peak,
                              "bytes_per_cell": bytes_cell, "peak_source": hbm_src,
                              # each field of a cell read once and written once (no ghosts): the
@@ -466,11 +568,28 @@ def run_reference(args):
           "sample": f"one SSP-RK3 step of {nsub} subgrids ({cells} cells) of the {args.workload} law per step"}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; {STEP}",
-                       "reference_sample": cb["sample"]},
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators of paper_2210_06439_gb300.inputs)",
+            "config": make_config(args, 1),
             "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
+
+
+def profile_rhs(args):
+    """args.reps RHS launches of one form on the workload, for a profiler."""
+    import torch
+    from paper_2210_06439_gb300 import binding, inputs
+    prob = WORKLOADS[args.workload][1](inputs)
+    H = binding.Hydro.from_problem(prob, precision=args.precision, recon=args.recon)
+    U = torch.from_numpy(prob.U).cuda()
+    H.fill_ghosts(U)
+    if args.autotune:
+        H.autotune(U)
+    d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+    for _ in range(args.reps):
+        H.rhs(U, d)
+    torch.cuda.synchronize()
+    assert H.error_flags() == 0
+    print("profile-rhs ok", args.workload, "precision", args.precision, "launch", H.launch_info())
 
 
 def main():
@@ -479,11 +598,21 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="periodic_box_64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="binary_star_256", choices=sorted(WORKLOADS))
     ap.add_argument("--recon", type=int, default=0, choices=(0, 1),
                     help="reconstructed variables: 0 the conserved fields (the method's default), 1 primitive")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--profile-rhs", action="store_true",
+                    help="only run --reps RHS launches of one form (for profiler captures); no benchmark line")
+    ap.add_argument("--precision", type=int, default=0, choices=(0, 1), help="form for --profile-rhs")
+    ap.add_argument("--reps", type=int, default=3, help="RHS launches for --profile-rhs")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false", help="--profile-rhs without autotuning")
     args = ap.parse_args()
+    if args.profile_rhs:
+        import __graft_entry__
+        __graft_entry__.build()
+        profile_rhs(args)
+        return
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

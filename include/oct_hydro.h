@@ -90,8 +90,12 @@ typedef enum { OCT_BC_GIVEN = 0, OCT_BC_PERIODIC = 1, OCT_BC_OUTFLOW = 2, OCT_BC
 typedef enum { OCT_RECON_CONSERVED = 0, OCT_RECON_PRIMITIVE = 1 } oct_recon;
 
 /* Device error flags (oct_hydro_get_error_flags). */
-#define OCT_FLAG_NONPHYS 0x1u /* rho <= 0 or non-finite value at a point   */
-#define OCT_FLAG_FLOOR 0x2u   /* a density, species or tau floor fired      */
+#define OCT_FLAG_NONPHYS 0x1u  /* rho <= 0 or non-finite value at a point   */
+#define OCT_FLAG_FLOOR 0x2u    /* a density, species or tau floor fired      */
+/* The uniform-level ghost fill met a ghost cell with no source (a diagonal
+ * neighbour missing where its face neighbours exist: an inconsistent
+ * neighbour table); that cell is left as it was. */
+#define OCT_FLAG_NO_SOURCE 0x4u
 
 /* Creates a handle for n_subgrids subgrids (Sec. II "Data-Structure": one
  * kernel invocation per set of subgrids with ghost layers).
@@ -106,7 +110,10 @@ typedef enum { OCT_RECON_CONSERVED = 0, OCT_RECON_PRIMITIVE = 1 } oct_recon;
  */
 oct_status oct_hydro_create(int n_subgrids, int edge, int ghost, int n_species, double gamma, oct_hydro_t *out);
 
-/* Sets the batch layout; all pointers are HOST pointers and are copied.
+/* Sets the batch layout (Sec. II "Data-Structure": the octree's leaves are
+ * subgrids of 8^3 cells with ghost layers, handed to the kernels in sets;
+ * Sec. III-D: one kernel call per set of subgrids).  All pointers are HOST
+ * pointers and are copied.
  *   edges      : n_subgrids edges in {8, 12, 16}; NULL = the create-time edge.
  *   offsets    : n_subgrids state offsets in doubles (multiples of 4, blocks
  *                not overlapping); NULL = packed in index order.
@@ -164,7 +171,10 @@ oct_status oct_hydro_set_prolongation(oct_hydro_t h, int order);
  * allocation-free entry point reconstructs the conserved fields only. */
 oct_status oct_hydro_set_reconstruction(oct_hydro_t h, int variables);
 
-/* Numerical parameters: precision (oct_precision: FP64 everywhere, or
+/* Numerical parameters (Sec. II "Solvers": the explicit finite-volume
+ * scheme and its CFL time step, Sec. V-A; the paper runs everything in FP64,
+ * Sec. V; the mixed form and the floors and dual-energy switches are
+ * readings of this library): precision (oct_precision: FP64 everywhere, or
  * reconstruction/flux arithmetic in FP32 with FP64 divergence, update,
  * floors and dt), CFL number (0 < cfl <= 1, default 0.4), density floor
  * (>= 0, default 1e-12) and the two dual-energy switches (default 1e-3 for
@@ -220,7 +230,11 @@ oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int n_steps, d
                                    void *cuda_stream);
 oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_host, void *cuda_stream);
 
-/* Times the candidate launch shapes of the RHS kernel on U_sample -- tile
+/* Chooses the work decomposition of the RHS kernel for this GPU (Sec. V-B:
+ * the paper splits its largest kernels into several tasks so that every
+ * core has work; here the unit is a column of cells of a subgrid, and the
+ * split is chosen by measurement).  Times the candidate launch shapes of the
+ * RHS kernel on U_sample -- tile
  * capacity and threads (8x8 cells per work item with 256, 512 or 1024
  * threads, or 8x4 with 256) x resident CTAs per SM (1 up to the occupancy
  * limit) -- and keeps the fastest for this layout, precision and
@@ -259,6 +273,24 @@ oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_species, dou
                                     double de_switch1, const double *U, const double *dx, double *dUdt, double *dt,
                                     void *cuda_stream);
 
+/* Diagnostics (the paper has no counterpart: they serve the measurements
+ * and tests of this library).
+ *
+ * oct_hydro_pipe_peaks: FP64 and FP32 FMA throughput of the current GPU in
+ * TFLOP/s (an FMA counts as two flops), each from one launch of independent
+ * FMA chains on a full grid lasting at least target_ms (0 < target_ms <=
+ * 10000), timed with CUDA events on the stream; synchronises it.  These are
+ * the measured peaks against which the benchmark reports its arithmetic-bound
+ * kernels.
+ *
+ * oct_hydro_eval_math: y[i] = fn(x[i]) for i < n on DEVICE arrays of doubles,
+ * stream-ordered, with fn the FP64 helpers the kernels use -- 0 the
+ * reciprocal, 1 the square root, 2 tau^gamma, 3 e^(1/gamma) -- or, for
+ * comparison, CUDA's own 1.0 / x (16), sqrt (17), pow(x, gamma) (18) and
+ * pow(x, 1.0 / gamma) (19).  OCT_E_ARG for another fn or NULL arrays. */
+oct_status oct_hydro_pipe_peaks(double target_ms, double *fp64_tflops, double *fp32_tflops, void *cuda_stream);
+oct_status oct_hydro_eval_math(int fn, const double *x, double *y, int64_t n, double gamma, void *cuda_stream);
+
 /* Launch shape of the RHS kernel for the current layout and precision
  * (the paper's Sec. V-B splits big kernels into tasks for the same reason:
  * enough independent work per core): tile mode (0: 8x8-cell columns with
@@ -269,7 +301,10 @@ oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_species, dou
  * decreasing work from a counter on the device.  Any pointer may be NULL. */
 oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *ctas_per_sm, int *n_items);
 
-/* Reads and clears the device error flags (OCT_FLAG_*); synchronises. */
+/* Reads and clears the device error flags (OCT_FLAG_*); synchronises.  The
+ * paper states no error handling; the flags report what readings R6 and R7
+ * of the floors and a non-physical point (rho <= 0, non-finite values) meet
+ * on the device, since a kernel does not trap. */
 oct_status oct_hydro_get_error_flags(oct_hydro_t h, uint32_t *flags);
 
 /* Text of the calling thread's last failed call ("" if none). */

@@ -18,7 +18,7 @@ OCT_OK, OCT_E_ARG, OCT_E_CUDA, OCT_E_NONPHYS, OCT_E_TIMEOUT, OCT_E_NOMEM, OCT_E_
 OCT_FP64, OCT_MIXED = 0, 1
 OCT_BC_GIVEN, OCT_BC_PERIODIC, OCT_BC_OUTFLOW, OCT_BC_AMR = 0, 1, 2, 3
 OCT_RECON_CONSERVED, OCT_RECON_PRIMITIVE = 0, 1
-OCT_FLAG_NONPHYS, OCT_FLAG_FLOOR = 0x1, 0x2
+OCT_FLAG_NONPHYS, OCT_FLAG_FLOOR, OCT_FLAG_NO_SOURCE = 0x1, 0x2, 0x4
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -45,6 +45,8 @@ SIGNATURES = {
     "oct_hydro_autotune": (_I, [_P, _P, _P]),
     "oct_hydro_rhs_dt_noalloc": (_I, [_I, _I, _I, _D, _I, _D, _D, _P, _P, _P, _P, _P]),
     "oct_hydro_launch_info": (_I, [_P, _P, _P, _P]),
+    "oct_hydro_pipe_peaks": (_I, [_D, _P, _P, _P]),
+    "oct_hydro_eval_math": (_I, [_I, _P, _P, _I64, _D, _P]),
     "oct_hydro_get_error_flags": (_I, [_P, _P]),
     "oct_hydro_last_error": (ctypes.c_char_p, []),
     "oct_hydro_destroy": (None, [_P]),
@@ -106,6 +108,21 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def pipe_peaks(target_ms=200.0, stream=None):
+    """(FP64, FP32) FMA throughput of the current GPU in TFLOP/s (an FMA
+    counts as two flops), each from one launch of at least target_ms."""
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    check(load().oct_hydro_pipe_peaks(float(target_ms), ctypes.addressof(f64), ctypes.addressof(f32),
+                                      _stream_ptr(stream)))
+    return f64.value, f32.value
+
+
+def eval_math(which, x, y, gamma=5.0 / 3.0, stream=None):
+    """y = fn(x) elementwise on device float64 tensors (oct_hydro_eval_math)."""
+    check(load().oct_hydro_eval_math(int(which), _ptr(x), _ptr(y), int(x.numel()), float(gamma),
+                                     _stream_ptr(stream)))
 
 
 class Hydro:

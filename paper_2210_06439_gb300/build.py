@@ -15,7 +15,7 @@ SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboct_hydro.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include", "oct_hydro.h")
-UNITS = ["oct_hydro.cu", "rhs_dispatch.cu"] + [f"rhs_{form}_m{mode}{rec}.cu" for rec in ("", "_prim")
+UNITS = ["oct_hydro.cu", "rhs_dispatch.cu", "diag.cu"] + [f"rhs_{form}_m{mode}{rec}.cu" for rec in ("", "_prim")
                                               for form in ("fp64", "mixed") for mode in (0, 1, 2, 3)]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

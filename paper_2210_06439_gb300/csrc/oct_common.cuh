@@ -116,6 +116,24 @@ __device__ __forceinline__ double rcp_nr(double x)
     return fma(r, e, r);
 }
 
+// sqrt(q): FP32 reciprocal-square-root estimate y (about 2^-22), s = q y,
+// then two Newton (Heron) corrections s <- s + (q - s^2) y / 2.
+__device__ __forceinline__ double sqrt_nr(double q)
+{
+    float qf;
+    if (!d2f_est(q, qf) || __double2hiint(q) < 0)  // negative: sqrt gives NaN
+        return sqrt(q);
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(qf));
+    double y = f2d_normal(yf);
+    double h = f2d_normal(0.5f * yf);
+    double s = q * y;
+    double r = fma(-s, s, q);
+    s = fma(r, h, s);
+    r = fma(-s, s, q);
+    return fma(r, h, s);
+}
+
 // tau^gamma, the internal energy that the entropy tracer gives where the
 // dual-energy switch selects it.  For gamma = 5/3 (the ideal monatomic gas of
 // every workload here): with tau = m 2^(3k), m in [1, 8) (exact, on the
@@ -152,6 +170,46 @@ __device__ __forceinline__ double eint_of_tau(double tau, double gamma)
     y = fma(-fma(y * y, y, -T), r, y);
     // y in [1, 32): scale by 2^(5k) on the exponent field (the result stays normal)
     return __hiloint2double(__double2hiint(y) + 5 * k * (1 << 20), __double2loint(y));
+}
+
+// e^(1/gamma), the entropy tracer of an internal energy e (the tau
+// re-synchronisation).  For gamma = 5/3 (the ideal monatomic gas of every
+// workload here): with e = m 2^(5k), m in [1, 32) (exact, on the exponent
+// field), e^(3/5) = m^(3/5) 2^(3k), and y = m^(3/5) solves y^5 = m^3 = T.
+// An FP32 estimate y0 = 2^(3/5 log2 m) (the hardware log2 and exp2
+// approximations; relative error below 1e-6 for every m) is refined by two
+// chord-Newton steps y <- y - (y^5 - T) r in FP64 with r = 1/(5 y0^4) from
+// FP32: each multiplies the relative error by about 1e-6, so the result is
+// within a couple of ulp whatever the magnitude of e.  Other gamma, e <= 0,
+// zero, subnormal, inf or NaN: pow, in a call of its own.
+static __device__ __noinline__ double pow_inv_rare(double x, double g) { return pow(x, 1.0 / g); }
+__device__ __forceinline__ double tau_of_eint(double e, double gamma)
+{
+    const int eh = __double2hiint(e);
+    if (__double_as_longlong(gamma) != __double_as_longlong(5.0 / 3.0) || eh < 0x00100000 || eh >= 0x7FF00000)
+        return pow_inv_rare(e, gamma);
+    const int eb = (eh >> 20) - 1023;  // unbiased exponent of a positive normal e
+    // k = floor(eb / 5), j = eb - 5k in 0..4
+    const int k = (eb >= 0 ? eb : eb - 4) / 5;
+    const int j = eb - 5 * k;
+    const double m = __hiloint2double((eh & 0x000FFFFF) | ((j + 1023) << 20), __double2loint(e));
+    const double T = m * m * m;
+    float mf;
+    d2f_est(m, mf);
+    float lf, yf, rf;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lf) : "f"(mf));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(lf * 0.6f));
+    const float y2f = yf * yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(5.0f * y2f * y2f));
+    const double r = f2d_normal(rf);
+    double y = f2d_normal(yf);
+#pragma unroll
+    for (int it = 0; it < 2; it++) {
+        const double y2 = y * y;
+        y = fma(-fma(y2 * y2, y, -T), r, y);
+    }
+    // y in [1, 8): scale by 2^(3k) on the exponent field (the result stays normal)
+    return __hiloint2double(__double2hiint(y) + 3 * k * (1 << 20), __double2loint(y));
 }
 
 }  // namespace octh

@@ -46,6 +46,9 @@ static oct_status fail(oct_status st, const char *fmt, ...)
     return st;
 }
 
+// For the other translation units of the library (diagnostics).
+oct_status octh_fail_text(oct_status st, const char *msg) { return fail(st, "%s", msg); }
+
 #define CUDA_TRY(call)                                                                                   \
     do {                                                                                                 \
         cudaError_t e_ = (call);                                                                         \

@@ -62,24 +62,6 @@ template <> struct Num<float> {
 // are refined by Newton-Raphson steps in FP64.
 // ---------------------------------------------------------------------------
 
-// sqrt(q): FP32 reciprocal-square-root estimate y (about 2^-22), s = q y,
-// then two Newton (Heron) corrections s <- s + (q - s^2) y / 2.
-__device__ __forceinline__ double sqrt_nr(double q)
-{
-    float qf;
-    if (!d2f_est(q, qf))
-        return sqrt(q);
-    float yf;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(qf));
-    double y = f2d_normal(yf);
-    double h = f2d_normal(0.5f * yf);
-    double s = q * y;
-    double r = fma(-s, s, q);
-    s = fma(r, h, s);
-    r = fma(-s, s, q);
-    return fma(r, h, s);
-}
-
 // The sign, zero and magnitude tests below work on the two 32-bit halves of
 // a double: written on the 64-bit pattern they would be recognised and issued
 // as FP64 compares and min/max, which is what they are meant to avoid.

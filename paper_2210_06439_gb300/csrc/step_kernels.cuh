@@ -65,21 +65,6 @@ struct CombineArgs {
     unsigned *flags;
 };
 
-// e^(1/gamma).  For gamma = 5/3 (the ideal monatomic gas of every workload
-// here) y = e^(3/5) solves y^5 = e^3: an FP32 estimate (powf, about 1e-7)
-// refined by one Newton step y <- (4 y + e^3 / y^4) / 5 in FP64, which
-// squares the relative error (about 1e-14 after it).  Other gamma: pow.
-__device__ __forceinline__ double tau_of_eint(double e, double gamma)
-{
-    float ef;
-    if (gamma == 5.0 / 3.0 && d2f_est(e, ef)) {
-        const double y = f2d_normal(powf(ef, 0.6f));
-        const double y2 = y * y;
-        return fma(4.0, y, e * e * e * rcp_nr(y2 * y2)) * 0.2;
-    }
-    return pow(e, 1.0 / gamma);
-}
-
 // One SSP-RK3 combine (Shu-Osher) on the interior, one thread per interior
 // cell of the whole batch (cell q of subgrid s at q - cell_begin[s]):
 //   stage 1: out = X + dt L                     (X = U0)
@@ -269,7 +254,7 @@ __global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf
                 U[di + f * FS] = v[f];
     }
     if (err)
-        atomicOr(flags, 4u);
+        atomicOr(flags, 4u);  // OCT_FLAG_NO_SOURCE
 }
 
 // Ghost fill across refinement levels from a host-built plan: entry q of

@@ -180,14 +180,12 @@ def _tile_global(name, fields, nsub, E, dxv, bc, periodic, gamma=GAMMA, meta=Non
     off, total = layout_offsets(edge, nf)
     U = np.zeros(total)
     B = E + 2 * NG
-    s = 0
-    for sz in range(nz):
-        for sy in range(ny):
-            for sx in range(nx):
-                blk = U[off[s]: off[s] + nf * B ** 3].reshape(nf, B, B, B)
-                blk[:, NG:NG + E, NG:NG + E, NG:NG + E] = fields[:, sz * E:(sz + 1) * E, sy * E:(sy + 1) * E,
-                                                                 sx * E:(sx + 1) * E]
-                s += 1
+    # one edge: block s at s * stride (layout_offsets), subgrids in x-fastest
+    # order; the interiors are copied in one strided assignment
+    stride = total // n
+    blocks = U.reshape(n, stride)[:, : nf * B ** 3].reshape(nz, ny, nx, nf, B, B, B)
+    blocks[:, :, :, :, NG:NG + E, NG:NG + E, NG:NG + E] = fields.reshape(nf, nz, E, ny, E, nx, E).transpose(
+        1, 3, 5, 0, 2, 4, 6)
     nbr = tiling_neighbours(nx, ny, nz, periodic)
     return Problem(name=name, edge=edge, off=off, dx=np.full(n, dxv), level=np.zeros(n, np.int32), nf=nf, U=U,
                    bc=bc, nbr=nbr, grid=(nx, ny, nz), gamma=gamma, meta=meta or {})

@@ -53,3 +53,28 @@ def interior_layout(U, prob):
         blk = U[prob.off[s]: prob.off[s] + prob.nf * B ** 3].reshape(prob.nf, B, B, B)
         out.append(blk[:, 3:3 + E, 3:3 + E, 3:3 + E].reshape(-1))
     return np.concatenate(out)
+
+
+def interior_view(U, prob):
+    """Interior cells of a uniform-edge, packed state array as a view
+    [subgrid, field, z, y, x] (no copy)."""
+    E = int(prob.edge[0])
+    assert np.all(prob.edge == E)
+    B = E + 6
+    n = prob.n_sub
+    stride = int(prob.off[1] - prob.off[0]) if n > 1 else prob.nf * B ** 3
+    assert int(prob.off[-1]) == (n - 1) * stride
+    V = U[: n * stride].reshape(n, stride)[:, : prob.nf * B ** 3].reshape(n, prob.nf, B, B, B)
+    return V[:, :, 3:3 + E, 3:3 + E, 3:3 + E]
+
+
+def state_field_errors(got, ref, prob):
+    """Per-field max |got - ref| over the interior of every subgrid, divided by
+    the field's max |ref| there (two state arrays of a uniform-edge batch)."""
+    G, R = interior_view(got, prob), interior_view(ref, prob)
+    errs = []
+    for f in range(prob.nf):
+        m = float(np.max(np.abs(R[:, f])))
+        d = float(np.max(np.abs(G[:, f] - R[:, f])))
+        errs.append(0.0 if d == 0 else (d / m if m > 0 else np.inf))
+    return np.array(errs)

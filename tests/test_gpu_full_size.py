@@ -9,11 +9,26 @@ import pytest
 
 import oracle
 from paper_2210_06439_gb300 import inputs
-from tests.helpers import e3s, field_errors, oracle_filled, MIXED_SPEED_RTOL
+from tests.helpers import e3s, field_errors, oracle_filled, state_field_errors, MIXED_SPEED_RTOL
 
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-12, 1: 1e-5}
+# the stepped state: FP64 as the RHS; the mixed form's RHS error enters the
+# state scaled by dt, held to the form's RHS bound
+STEP_TOL = {0: 1e-12, 1: 1e-5}
+
+
+def _rhs_field_errors(g, o, prob):
+    """Per-field max relative error of two RHS arrays of a uniform-edge batch."""
+    G = g.reshape(prob.n_sub, prob.nf, -1)
+    O = o.reshape(prob.n_sub, prob.nf, -1)
+    errs = []
+    for f in range(prob.nf):
+        m = float(np.max(np.abs(O[:, f])))
+        d = float(np.max(np.abs(G[:, f] - O[:, f])))
+        errs.append(0.0 if d == 0 else (d / m if m > 0 else np.inf))
+    return np.array(errs)
 
 
 def _setup(prob, precision, fill=True):
@@ -71,57 +86,102 @@ def test_periodic_box_64_autotuned(precision):
     np.testing.assert_allclose(am_g, am_o, rtol=1e-12 if precision == 0 else MIXED_SPEED_RTOL)
 
 
-def test_mixed_levels_4096_sampled():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mixed_levels_4096_sampled(precision):
+    """The 4096-subgrid batch of edges 8/12/16 on three levels in one
+    persistent launch.  FP64: sampled cells at 1e-11 of each cell's scale;
+    mixed form: per field, the max error over 600 sampled cells divided by
+    the field's max |oracle| over them, at the form's 1e-5."""
     p = inputs.mixed_levels()
-    H, U, st = _setup(p, 0, fill=False)
+    H, U, st = _setup(p, precision, fill=False)
     d_g, am_g = _rhs(H, U, st, p.n_sub)
     assert H.error_flags() == 0
-    _sample_check(p, d_g)
+    if precision == 0:
+        _sample_check(p, d_g)
+    else:
+        rng = np.random.default_rng(11)
+        s = rng.integers(0, p.n_sub, 600)
+        c = np.array([rng.integers(0, int(p.edge[k]) ** 3) for k in s])
+        smp = np.stack([s, c], axis=1)
+        ref = oracle.rhs_cells(p.edge, p.off, p.dx, p.nf, p.U, smp, gamma=p.gamma)
+        doff = np.concatenate([[0], np.cumsum(p.nf * p.edge.astype(np.int64) ** 3)])
+        got = np.stack([d_g[doff[k] + cc + int(p.edge[k]) ** 3 * np.arange(p.nf)] for k, cc in smp])
+        errs = np.max(np.abs(got - ref), axis=0) / np.max(np.abs(ref), axis=0)
+        print("\nmixed_levels mixed form, sampled max rel err per field:", " ".join(f"{e:.2e}" for e in errs))
+        assert np.all(errs <= TOL[1]), errs
     # signal speeds of a few whole subgrids
     for s in (0, 1, 2, 4095):
         q = p.copy()
         _, am_o, _ = oracle.rhs(q.edge[s:s + 1], q.off[s:s + 1], q.dx[s:s + 1], q.nf, q.U)
-        assert am_g[s] == pytest.approx(am_o[0], rel=1e-12)
+        assert am_g[s] == pytest.approx(am_o[0], rel=1e-12 if precision == 0 else MIXED_SPEED_RTOL)
 
 
-def test_binary_star_128_fp64_and_mixed_error_table():
-    p = inputs.binary_star(16)
-    ref = oracle_filled(p)
-    d_o, am_o, nb = oracle.rhs(ref.edge, ref.off, ref.dx, ref.nf, ref.U)
+def _binary_star_rhs_and_step(nsub):
+    """Every cell of the binary-star box: the RHS and one RK3 step (replayed
+    from the captured graph on a side stream, autotuned launch shape), in
+    both forms, against the FP64 oracle.  The oracle fills its own ghosts
+    (outflow edges) and steps its own copy."""
+    import torch
+    p = inputs.binary_star(nsub)
+    U_init = torch.from_numpy(p.U).cuda()  # ghosts still empty: each handle fills them
+    oracle.ghost_fill(8, p.off, p.nf, p.nbr, p.U)  # p.U: the oracle's filled initial state
+    d_o, am_o, nb = oracle.rhs(p.edge, p.off, p.dx, p.nf, p.U)
     assert nb == 0
     rows = {}
     for prec in (0, 1):
-        H, U, st = _setup(p, prec)
+        H, U, st = _setup(p, prec, fill=False)
+        U.copy_(U_init)
+        H.fill_ghosts(U, stream=st)
         d_g, am_g = _rhs(H, U, st, p.n_sub)
         assert H.error_flags() == 0
-        rows[prec] = field_errors(d_g, d_o, p.nf, e3s(p))
+        rows[prec] = _rhs_field_errors(d_g, d_o, p)
         np.testing.assert_allclose(am_g, am_o, rtol=1e-12 if prec == 0 else MIXED_SPEED_RTOL)
+        H.close()
+        del H, U, d_g
+    del d_o
+    dt_o, fired, rc = oracle.rk3_step(p.edge, p.off, p.dx, p.nf, p.U, bc=2, nbr=p.nbr)
+    assert rc == 0
+    step = {}
+    for prec in (0, 1):
+        H, U, st = _setup(p, prec, fill=False)
+        U.copy_(U_init)
+        H.fill_ghosts(U, stream=st)
+        dt_g = H.rk_step(U, stream=st)
+        flags = H.error_flags()
+        assert not flags & 1
+        if prec == 0:
+            assert bool(flags & 2) == (fired > 0)
+        assert dt_g == pytest.approx(dt_o, rel=1e-12 if prec == 0 else MIXED_SPEED_RTOL)
+        step[prec] = state_field_errors(U.cpu().numpy(), p.U, p)
+        H.close()
+        del H, U
     names = ["rho", "sx", "sy", "sz", "E", "tau", "r1", "r2", "r3", "r4", "r5"]
-    print("\nbinary_star_128 max rel err per field (FP64 | mixed):")
+    print(f"\nbinary_star {8 * nsub}^3 max rel err per field, RHS FP64 | mixed, RK3 step FP64 | mixed "
+          f"(oracle floor firings {fired}):")
     for f in range(p.nf):
-        print(f"  {names[f]:4s} {rows[0][f]:.2e} | {rows[1][f]:.2e}")
+        print(f"  {names[f]:4s} {rows[0][f]:.2e} | {rows[1][f]:.2e}   {step[0][f]:.2e} | {step[1][f]:.2e}")
     assert np.all(rows[0] <= TOL[0]) and np.all(rows[1] <= TOL[1])
+    assert np.all(step[0] <= STEP_TOL[0]) and np.all(step[1] <= STEP_TOL[1])
+
+
+def test_binary_star_128_rhs_and_rk3_step_every_cell():
+    _binary_star_rhs_and_step(16)
+
+
+def test_binary_star_256_rhs_and_rk3_step_every_cell():
+    _binary_star_rhs_and_step(32)
 
 
 def test_binary_star_256_graph_100_steps():
+    """100 RK3 steps from the captured graph in each form: the stability
+    check of the 256^3 binary star (reading c9).  No non-physical state may
+    appear; the floors (species and density at the stellar surfaces) may
+    fire, and are counted by the flag word only."""
     import torch
-    p = inputs.binary_star(32)
-    # RHS parity on the initial state at sampled cells (oracle fills its own ghosts)
-    ref = oracle_filled(p)
-    H, U, st = _setup(p, 0)
-    d_g, _ = _rhs(H, U, st, p.n_sub)
-    assert H.error_flags() == 0
-    _sample_check(ref, d_g, n=200)
-    del d_g, ref
-    # 100 RK3 steps from the captured graph in each form: the stability check
-    # of the 256^3 binary star.  No non-physical state may appear; the floors
-    # (species and density at the stellar surfaces) may fire, and are counted
-    # by the flag word only.
     from paper_2210_06439_gb300 import binding
+    p = inputs.binary_star(32)
     for prec in (0, 1):
-        if prec == 1:
-            H.close()
-            H, U, st = _setup(p, 1)
+        H, U, st = _setup(p, prec)
         mass0 = float(torch.sum(U).item())
         dts = []
         for k in range(100):
@@ -136,3 +196,5 @@ def test_binary_star_256_graph_100_steps():
         assert all(d > 0 and math.isfinite(d) for d in dts)
         assert torch.isfinite(U).all().item()
         assert math.isfinite(float(torch.sum(U).item())) and mass0 > 0
+        H.close()
+        del H, U

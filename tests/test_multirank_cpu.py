@@ -72,7 +72,8 @@ def test_reference_arm_prints_the_contract_line():
         assert k in d, k
     assert d["value"] > 0 and d["ms_per_step"] > 0 and d["steps"] == 1 and d["warmup"] >= 3
     assert d["higher_is_better"] is True and d["n_gpus"] == 1
-    assert d["config"]["workload"].startswith("periodic_box_64")
+    assert d["config"]["workload"].startswith("binary_star_256")
+    assert d["config"]["interior_cells"] == 256 ** 3 and d["config"]["subgrids"] == 32768
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e = d["e2e"]
