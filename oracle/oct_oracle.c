@@ -52,7 +52,10 @@
  *       w = (rho, v, p, tau, X_i = rho_i / rho) of every cell, and each point
  *       is turned back into conserved fields (s = rho v,
  *       E = p / (gamma - 1) + rho |v|^2 / 2, rho_i = rho X_i) with its v, p
- *       taken as reconstructed; the cell's p uses the dual-energy switch.
+ *       taken as reconstructed; the cell's p uses the dual-energy switch;
+ *   R18 gravity, same-level monopole interactions: each cell receives
+ *       -G m_j / r and -G m_j (x_i - x_j) / r^3 from every cell j of its
+ *       level within r_s cell widths, m_j = rho_j dx^3 at the cell centre.
  *
  * Field order: rho, s_x, s_y, s_z, E_gas, tau, rho_1 .. rho_ns.
  * State layout: one ghosted block per subgrid, structure of arrays
@@ -1200,4 +1203,81 @@ int oco_amr_ghost_fill_order(int n_sub, int E, const int64_t *off, int nf, const
     free(src_c);
     free(par);
     return err ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gravity: same-level monopole interactions (reading R18)                   */
+/* ------------------------------------------------------------------------ */
+
+/* The gravity solver's most compute-intensive step is the same-level
+ * interaction between close-by cells; for non-refined cells it is the
+ * "monopole" kernel (Sec. II "Solvers", Sec. IV).  Reading R18: on one level
+ * of cell width dx, every interior cell i receives the potential and the
+ * acceleration of every cell j of the same level within the interaction
+ * radius, 0 < |x_j - x_i| <= r_s dx, each taken as a point mass
+ * m_j = rho_j dx^3 at its centre (Newtonian gravity, constant G):
+ *     phi_i = -G sum_j m_j / r_ij,
+ *     g_i   = -G sum_j m_j (x_i - x_j) / r_ij^3,   r_ij = |x_i - x_j|.
+ * Cells j are integer offsets d = (j - i) with d.d <= r_s^2, visited z
+ * outermost, then y, then x, each from -R to R (R = floor(r_s) <= E); a
+ * source cell is found in the subgrid itself or through the neighbour table
+ * (as for the ghost fill; a missing neighbour holds no mass).  rho is field 0
+ * of the ghosted state; all subgrids share edge E and the cell width dx.
+ * Output: phi [subgrid][E^3], g [subgrid][3][E^3] (x, y, z).
+ * Returns 0, or -1 for bad arguments. */
+int oco_gravity_monopole(int n_sub, int E, const int64_t *off, int nf, const int32_t *nbr, double dx, double G,
+                         double r_s, const double *U, double *phi, double *g)
+{
+    if (!valid_edge(E) || !(r_s >= 1.0) || (int)floor(r_s) > E || !(dx > 0.0))
+        return -1;
+    const int R = (int)floor(r_s);
+    const int B = E + 2 * NG;
+    const int64_t E3 = (int64_t)E * E * E;
+    const double r2max = r_s * r_s;
+    const double dx3 = dx * dx * dx;
+    (void)nf;
+#pragma omp parallel for schedule(dynamic)
+    for (int s = 0; s < n_sub; s++) {
+        for (int z = 0; z < E; z++)
+            for (int y = 0; y < E; y++)
+                for (int x = 0; x < E; x++) {
+                    double p = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+                    for (int dz = -R; dz <= R; dz++)
+                        for (int dy = -R; dy <= R; dy++)
+                            for (int ddx = -R; ddx <= R; ddx++) {
+                                if (dz == 0 && dy == 0 && ddx == 0)
+                                    continue;
+                                const double d2 = (double)(ddx * ddx + dy * dy + dz * dz);
+                                if (d2 > r2max)
+                                    continue;
+                                /* the source cell: its subgrid and local coordinates */
+                                int c[3] = {x + ddx, y + dy, z + dz}, o[3];
+                                for (int a = 0; a < 3; a++) {
+                                    o[a] = c[a] < 0 ? -1 : (c[a] >= E ? 1 : 0);
+                                    c[a] -= o[a] * E;
+                                }
+                                int src = s;
+                                if (o[0] || o[1] || o[2]) {
+                                    src = nbr[26 * (int64_t)s + nb_index(o[0], o[1], o[2])];
+                                    if (src < 0)
+                                        continue;
+                                }
+                                const double rho = U[off[src] + cidx(B, c[0] + NG, c[1] + NG, c[2] + NG)];
+                                const double m = rho * dx3;
+                                const double r = sqrt(d2) * dx;
+                                const double r3 = r * r * r;
+                                p -= G * m / r;
+                                /* x_i - x_j = -d dx */
+                                gx -= G * m * (-ddx * dx) / r3;
+                                gy -= G * m * (-dy * dx) / r3;
+                                gz -= G * m * (-dz * dx) / r3;
+                            }
+                    const int64_t q = ((int64_t)z * E + y) * E + x;
+                    phi[(int64_t)s * E3 + q] = p;
+                    g[(int64_t)s * 3 * E3 + q] = gx;
+                    g[(int64_t)s * 3 * E3 + E3 + q] = gy;
+                    g[(int64_t)s * 3 * E3 + 2 * E3 + q] = gz;
+                }
+    }
+    return 0;
 }

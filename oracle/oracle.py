@@ -19,7 +19,7 @@ _OUT = os.path.join(_HERE, "_build", "liboct_oracle.so")
 __all__ = [
     "build_oracle", "lib", "ppm", "prim", "kt_point", "simpson", "rhs", "rhs_cells",
     "dt_from_amax", "ghost_fill", "floors", "rk_combine", "rk3_step", "max_threads", "amr_ghost_fill",
-    "rk3_step_amr", "rhs_faces", "amr_reflux",
+    "rk3_step_amr", "rhs_faces", "amr_reflux", "gravity_monopole",
 ]
 
 _lib = None
@@ -57,6 +57,8 @@ _P = ctypes.c_void_p
 
 
 def _declare(L):
+    L.oco_gravity_monopole.argtypes = [_I, _I, _P, _I, _P, _D, _D, _D, _P, _P, _P]
+    L.oco_gravity_monopole.restype = _I
     L.oco_ppm.argtypes = [_P, _P, _P]
     L.oco_prim.argtypes = [_P, _D, _D, _P, _P, _P]
     L.oco_prim.restype = _I
@@ -283,3 +285,18 @@ def rk3_step_amr(edge, off, dx, nf, U, level, origin, n0, periodic, gamma=5.0 / 
                                       rho_floor, cfl, float(dt_cap), _p(lev), _p(org), int(n0), int(periodic),
                                       int(order), _p(U), U.size, _p(dt), _p(fired), int(nthreads))
     return float(dt[0]), int(fired[0]), int(st)
+
+
+def gravity_monopole(E, off, nf, nbr, dx, U, G=1.0, r_s=2.0 / 0.34):
+    """Same-level monopole interactions (reading R18) of a uniform-edge batch
+    with a neighbour table: returns (phi [n_sub * E^3], g [n_sub * 3 * E^3])."""
+    off, nbr = _i64(off), _i32(nbr)
+    assert U.dtype == np.float64 and U.flags.c_contiguous
+    n = off.shape[0]
+    phi = np.zeros(n * E ** 3)
+    g = np.zeros(3 * n * E ** 3)
+    r = lib().oco_gravity_monopole(n, int(E), _p(off), int(nf), _p(nbr), float(dx), float(G), float(r_s), _p(U),
+                                   _p(phi), _p(g))
+    if r != 0:
+        raise ValueError("oracle gravity_monopole: bad arguments")
+    return phi, g
