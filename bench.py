@@ -144,13 +144,17 @@ LINES = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 
          (1, 1, 1), (1, -1, -1), (1, -1, 1), (1, 1, -1)]
 
 
-def constant_stencils(U, prob):
-    """(PPM line evaluations counted by rhs_counts, how many of them have a
-    5-cell stencil of one value) over one RHS of the state U (a CUDA tensor
-    in the ghosted layout; uniform edge only, else None).  The FP64 kernel
-    returns such a stencil's own value without any slope arithmetic, so the
-    work it does on a state with uniform regions (the binary star's
-    atmosphere, the Sedov ambient gas) is the method's count minus these.
+def skipped_work(U, prob):
+    """What the RHS kernels leave out on the state U (a CUDA tensor in the
+    ghosted layout; uniform edge only, else None), as (uniform subgrids,
+    PPM line evaluations counted by rhs_counts in the other subgrids, how many
+    of those have a 5-cell stencil of one value).
+      - A subgrid whose whole ghosted block holds one value per field: every
+        face flux is the same, its RHS is zero and a_max follows from the one
+        state; the kernels write both without reconstruction or fluxes (the
+        8x8 tiles of edge 8 are whole subgrids).
+      - Elsewhere the FP64 kernel returns a stencil of one value as its own
+        reconstruction without slope arithmetic.
     Counted cells as in rhs_counts: all 13 lines of every interior cell, the
     9 lines with a step across a face for each cell just outside it."""
     import torch
@@ -162,11 +166,17 @@ def constant_stencils(U, prob):
     if any(int(prob.off[s]) != s * stride for s in (0, n - 1)):
         return None
     V = U[: n * stride].view(n, stride)[:, : nf * B ** 3].view(n, nf, B, B, B)
+    uniform = torch.ones(n, dtype=torch.bool, device=U.device)
+    for f in range(nf):
+        X = V[:, f]
+        uniform &= (X == X[:, :1, :1, :1]).flatten(1).all(dim=1)
+    live = (~uniform)[:, None, None, None]
     R = E + 2  # cells -1 .. E per axis
     r = torch.arange(R, device=U.device)
     inner = (r >= 1) & (r <= E)
     ring = ~inner
     total = nconst = 0
+    n_live = int((~uniform).sum().item())
     for d in LINES:
         dx, dy, dz = d
         m = inner[:, None, None] & inner[None, :, None] & inner[None, None, :]
@@ -176,7 +186,7 @@ def constant_stencils(U, prob):
             m = m | (inner[:, None, None] & ring[None, :, None] & inner[None, None, :])
         if dz:
             m = m | (ring[:, None, None] & inner[None, :, None] & inner[None, None, :])
-        total += int(m.sum().item()) * n * nf
+        total += int(m.sum().item()) * n_live * nf
         for f in range(nf):
             X = V[:, f]
             c0 = X[:, 2:2 + R, 2:2 + R, 2:2 + R]
@@ -185,8 +195,18 @@ def constant_stencils(U, prob):
                 sl = X[:, 2 + k * dz:2 + k * dz + R, 2 + k * dy:2 + k * dy + R, 2 + k * dx:2 + k * dx + R]
                 eq = sl == c0
                 const = eq if const is None else const & eq
-            nconst += int((const & m).sum().item())
-    return total, nconst
+            nconst += int((const & m & live).sum().item())
+    return n - n_live, total, nconst
+
+
+GRAV_RS = 2.0 / 0.34  # same-level interaction radius (cell widths) for the paper's opening angle
+
+
+def grav_pairs(r_s):
+    """Cells j != i of a cell's stencil: integer offsets with |d|^2 <= r_s^2."""
+    R = int(math.floor(r_s))
+    return sum(1 for dz in range(-R, R + 1) for dy in range(-R, R + 1) for dx in range(-R, R + 1)
+               if 0 < dx * dx + dy * dy + dz * dz <= r_s * r_s)
 
 
 def bound_of(alu_frac, hbm_frac):
@@ -348,6 +368,19 @@ def run_ours(args, rank, world):
         results[prec] = dict(step_ms=step_ms, rhs_ms=rhs_ms, flags=flags, H=H, U=U, dU=dU, U0=U0,
                              launch=H.launch_info())
 
+    # same-level monopole gravity (a separate solver step, not part of the
+    # hydro RK3 step): its kernel alone, on the FP64 handle's state
+    grav = None
+    if prob.bc in (1, 2):
+        H64g, U64g = results[binding.OCT_FP64]["H"], results[binding.OCT_FP64]["U0"]
+        E3 = int(prob.edge[0]) ** 3
+        phi = torch.empty(prob.n_sub * E3, dtype=torch.float64, device="cuda")
+        gacc = torch.empty(3 * prob.n_sub * E3, dtype=torch.float64, device="cuda")
+        grav_ms = timed(lambda: H64g.gravity_monopole(U64g, phi, gacc, G=1.0, r_s=GRAV_RS, stream=stream),
+                        max(3, min(args.steps, 5)), args.warmup)
+        grav = reduce_max(statistics.mean(grav_ms), world)
+        del phi, gacc
+
     # end to end through the host-buffer ABI call (pinned host state)
     H64 = results[binding.OCT_FP64]["H"]
     Uh = torch.from_numpy(prob.U.copy()).pin_memory()
@@ -372,8 +405,8 @@ def run_ours(args, rank, world):
     mixed_err = None
     if args.cpu_baseline and rank == 0 and prob.n_cells <= 2 ** 21:
         mixed_err = mixed_error_table(prob, results, stream)
-    # the FP64 RHS was timed on U0: the stencils its kernel skips there
-    cst = constant_stencils(s64["U0"], prob) if rank == 0 else None
+    # the RHS was timed on U0: the work its kernels skip there
+    skip = skipped_work(s64["U0"], prob) if rank == 0 else None
     # measured FMA peaks of this GPU (one launch of >= 200 ms each, as long as
     # the FP64 RHS launch of the largest workloads)
     with torch.cuda.stream(stream):
@@ -386,13 +419,15 @@ def run_ours(args, rank, world):
     assert config["interior_cells"] == n_cells and config["subgrids"] == prob.n_sub
     value, ms_step = aggregate(n_cells, world, tot64, K)
     ops_cell, bytes_cell = problem_counts(prob)
-    ops_eff = ops_cell
-    if cst is not None:
-        ops_eff = ops_cell - cst[1] * OPS_PPM / n_cells
+    ops_eff = ops_mx = ops_cell
+    if skip is not None:
+        live = 1.0 - skip[0] * int(prob.edge[0]) ** 3 / n_cells  # cells outside uniform subgrids
+        ops_mx = ops_cell * live
+        ops_eff = ops_mx - skip[2] * OPS_PPM / n_cells
     hbm_peak, hbm_src = _peaks()
     rhs_tflops = ops_eff * n_cells / (rhs64 * 1e-3) / 1e12
     rhs_gbs = bytes_cell * n_cells / (rhs64 * 1e-3) / 1e9
-    mx_tflops = ops_cell * n_cells / (rhsmx * 1e-3) / 1e12
+    mx_tflops = ops_mx * n_cells / (rhsmx * 1e-3) / 1e12
     mx_gbs = bytes_cell * n_cells / (rhsmx * 1e-3) / 1e9
     state_bytes = prob.U.nbytes
     out = {
@@ -413,7 +448,8 @@ def run_ours(args, rank, world):
         "mixed": {"value": world * n_cells / (totmx / K * 1e-3), "unit": UNIT, "ms_per_step": totmx / K,
                   "rhs_value": world * n_cells / (rhsmx * 1e-3), "rhs_ms": rhsmx,
                   "speedup_vs_fp64_step": ms_step / (totmx / K), "speedup_vs_fp64_rhs": rhs64 / rhsmx,
-                  "rhs_roofline": {"bound": bound_of(mx_tflops / f32_peak, mx_gbs / hbm_peak),
+                  "rhs_roofline": {"ops_per_cell": ops_mx,
+                                   "bound": bound_of(mx_tflops / f32_peak, mx_gbs / hbm_peak),
                                    "achieved": mx_tflops, "peak": f32_peak, "unit": "TFLOP/s",
                                    "frac": mx_tflops / f32_peak, "peak_source": "measured (FFMA loop, this process)",
                                    "hbm_gbs": mx_gbs, "hbm_frac": mx_gbs / hbm_peak}},
@@ -423,9 +459,11 @@ def run_ours(args, rank, world):
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "kernel": "rhs_kernel<double> (FP64 RHS)",
                      "ops_per_cell": ops_eff, "method_ops_per_cell": ops_cell,
-                     "ops_note": "FP64 flops of the method's formulas per interior cell, less the PPM lines whose "
-                                 "5-cell stencil holds one value (the kernel returns that value without slope "
-                                 "arithmetic)" + (f": {cst[1]} of {cst[0]} line evaluations" if cst else ""),
+                     "ops_note": "FP64 flops of the method's formulas per interior cell, less the work the kernel "
+                                 "leaves out: subgrids whose ghosted block holds one value per field (RHS zero, "
+                                 "written directly) and, elsewhere, the PPM lines whose 5-cell stencil holds one "
+                                 "value" + (f": {skip[0]} of {prob.n_sub} subgrids uniform, {skip[2]} of {skip[1]} "
+                                            "line evaluations in the others constant" if skip else ""),
                      "peak_source": "measured (DFMA loop, this process)",
                      "fp64_peak_tflops": f64_peak, "fp32_peak_tflops": f32_peak,
                      "hbm": {"achieved": rhs_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": rhs_gbs / hbm_peak,
@@ -443,6 +481,14 @@ def run_ours(args, rank, world):
         "launch": {k: {"tile_mode": r["launch"][0], "ctas_per_sm": r["launch"][1], "work_items": r["launch"][2]}
                    for k, r in (("fp64", s64), ("mixed", smx))},
     }
+    if grav is not None:
+        pairs = grav_pairs(GRAV_RS)
+        gt = 8.0 * pairs * n_cells / (grav * 1e-3) / 1e12
+        out["gravity_monopole"] = {
+            "ms": grav, "unit": "ms per launch", "r_s": GRAV_RS, "pairs_per_cell": pairs,
+            "roofline": {"bound": "alu", "achieved": gt, "peak": f64_peak, "unit": "TFLOP/s", "frac": gt / f64_peak,
+                         "work": "4 FP64 FMAs (8 flops) per interacting pair: the potential and three field "
+                                 "components from one mass and the stencil's 1/|d|, d/|d|^3"}}
     if mixed_err is not None:
         out["mixed"]["max_rel_err_per_field_vs_oracle"] = mixed_err
     if args.cpu_baseline:

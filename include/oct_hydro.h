@@ -273,6 +273,27 @@ oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_species, dou
                                     double de_switch1, const double *U, const double *dx, double *dUdt, double *dt,
                                     void *cuda_stream);
 
+/* Gravity, same-level monopole interactions (Sec. II "Solvers": the gravity
+ * solver's most compute-intensive step is the interaction between close-by
+ * cells of one level; for non-refined cells it is the monopole kernel).  The
+ * paper gives no equations; the reading used: every interior cell i receives
+ * from each cell j of its level within r_s cell widths (0 < |d| <= r_s,
+ * d = j - i in cells) the potential and acceleration of a point mass
+ * m_j = rho_j dx^3 at the cell centre,
+ *     phi_i = -G sum_j m_j / r_ij,   g_i = -G sum_j m_j (x_i - x_j) / r_ij^3,
+ * with rho field 0 of the state U (interiors only: the subgrid's own and its
+ * neighbours' through the neighbour table; a missing neighbour holds no
+ * mass).  For the paper's opening angle theta = 0.34, r_s = 2 / theta.
+ * Needs the periodic or outflow layout (one edge, a neighbour table) and one
+ * cell width for every subgrid; 1 <= r_s <= edge, and the subgrid with its
+ * halo of floor(r_s) cells plus the stencil must fit in shared memory
+ * (edge 8: r_s < 9; OCT_E_ARG otherwise).  G > 0.
+ * Output (device): phi [subgrid][edge^3], g [subgrid][3][edge^3] (x, y, z).
+ * A call with a new r_s rebuilds the stencil (a synchronous copy); the
+ * launch itself is stream-ordered. */
+oct_status oct_hydro_gravity_monopole(oct_hydro_t h, const double *U, double G, double r_s, double *phi, double *g,
+                                      void *cuda_stream);
+
 /* Diagnostics (the paper has no counterpart: they serve the measurements
  * and tests of this library).
  *

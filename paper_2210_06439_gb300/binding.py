@@ -45,6 +45,7 @@ SIGNATURES = {
     "oct_hydro_autotune": (_I, [_P, _P, _P]),
     "oct_hydro_rhs_dt_noalloc": (_I, [_I, _I, _I, _D, _I, _D, _D, _P, _P, _P, _P, _P]),
     "oct_hydro_launch_info": (_I, [_P, _P, _P, _P]),
+    "oct_hydro_gravity_monopole": (_I, [_P, _P, _D, _D, _P, _P, _P]),
     "oct_hydro_pipe_peaks": (_I, [_D, _P, _P, _P]),
     "oct_hydro_eval_math": (_I, [_I, _P, _P, _I64, _D, _P]),
     "oct_hydro_get_error_flags": (_I, [_P, _P]),
@@ -226,6 +227,12 @@ class Hydro:
 
     def rhs_host(self, U_host, dUdt_host, stream=None):
         check(self.L.oct_hydro_rhs_host(self.h, _ptr(U_host), _ptr(dUdt_host), _stream_ptr(stream)))
+
+    def gravity_monopole(self, U, phi, g, G=1.0, r_s=2.0 / 0.34, stream=None):
+        """Same-level monopole gravity of the state U into phi [n * E^3] and
+        g [n * 3 * E^3] (device float64 tensors)."""
+        check(self.L.oct_hydro_gravity_monopole(self.h, _ptr(U), float(G), float(r_s), _ptr(phi), _ptr(g),
+                                                _stream_ptr(stream)))
 
     def autotune(self, U, stream=None):
         check(self.L.oct_hydro_autotune(self.h, _ptr(U), _stream_ptr(stream)))

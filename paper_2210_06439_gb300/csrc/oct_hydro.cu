@@ -20,6 +20,7 @@
 #include "oct_common.cuh"
 #include "rhs_launch.h"
 #include "step_kernels.cuh"
+#include "gravity.cuh"
 
 namespace {
 // An NVTX range around each ABI call that launches work, so that timelines
@@ -81,7 +82,6 @@ struct oct_hydro {
     std::vector<int> item_begin;
     std::vector<int> order;             // execution order of the items (empty: index order)
     int items_mode = -1, items_grid = 0;  // the launch shape the items were cut for
-    std::vector<long long> cell_begin;  // packed interior-cell offset of each subgrid
     long long state_len = 0, rhs_len = 0;
     // launch shape: 0 8x8 tiles (6x6 for edge 12), 256 threads; 1 8x4 tiles (6x4
     // for edge 12), 256 threads; 2 8x8 tiles, 512 threads; 3 8x8 tiles, 1024 threads
@@ -93,7 +93,7 @@ struct oct_hydro {
     double *d_Wprim = nullptr;   // primitive variables of the state (primitive reconstruction)
     // device memory
     int *d_edge = nullptr, *d_nbr = nullptr, *d_item_begin = nullptr;
-    long long *d_off = nullptr, *d_doff = nullptr, *d_cell_begin = nullptr;
+    long long *d_off = nullptr, *d_doff = nullptr;
     double *d_dx = nullptr;
     WorkItem *d_items = nullptr;
     int *d_order = nullptr;   // execution order (null: index order)
@@ -113,6 +113,11 @@ struct oct_hydro {
     int *d_corr_first = nullptr;
     int n_corr_cells = 0;
     std::map<const double *, GraphEntry> graphs;
+    // same-level monopole gravity: the stencil for the radius last used
+    int *d_gst_off = nullptr;
+    GravEntry *d_gst_k = nullptr;
+    int gst_n = 0, gst_S = 0;
+    double gst_rs = 0.0;
 };
 
 template <class P>
@@ -155,7 +160,6 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_item_begin);
     dfree(h->d_off);
     dfree(h->d_doff);
-    dfree(h->d_cell_begin);
     dfree(h->d_dx);
     dfree(h->d_items);
     dfree(h->d_order);
@@ -445,11 +449,6 @@ extern "C" oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, 
     CUDA_TRY(cudaMemcpy(h->d_off, off.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&h->d_doff, sizeof(long long) * n));
     CUDA_TRY(cudaMemcpy(h->d_doff, doff.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
-    h->cell_begin.resize(n);
-    for (int s = 0; s < n; s++)
-        h->cell_begin[s] = doff[s] / nf;
-    CUDA_TRY(cudaMalloc(&h->d_cell_begin, sizeof(long long) * n));
-    CUDA_TRY(cudaMemcpy(h->d_cell_begin, h->cell_begin.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
     if (!nb.empty()) {
         CUDA_TRY(cudaMalloc(&h->d_nbr, sizeof(int) * nb.size()));
         CUDA_TRY(cudaMemcpy(h->d_nbr, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice));
@@ -964,8 +963,9 @@ static oct_status launch_combine(oct_hydro *h, int stage, const double *U0, cons
     A.rho_floor = h->rho_floor;
     A.eps2 = h->eps2;
     A.flags = h->d_flags;
-    const long long n_cells = h->rhs_len / h->nf;
-    combine_kernel<<<(unsigned)((n_cells + 255) / 256), 256, 0, s>>>(A, h->n_sub, h->d_cell_begin, n_cells);
+    // two blocks of 256 threads per subgrid: one cell a thread for edge 8
+    constexpr int parts = 2;
+    combine_kernel<<<(unsigned)(h->n_sub * parts), 256, 0, s>>>(A, parts);
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;
 }
@@ -1253,7 +1253,91 @@ extern "C" void oct_hydro_destroy(oct_hydro_t h)
     dfree(h->d_dt);
     dfree(h->d_dtcap);
     dfree(h->d_ticket);
+    dfree(h->d_gst_off);
+    dfree(h->d_gst_k);
     delete h;
+}
+
+// Raises the monopole kernel's dynamic shared-memory limit on the current
+// device to at least bytes (never lowers it: other handles may need more).
+static cudaError_t monopole_smem_limit(size_t bytes)
+{
+    static std::mutex mu;
+    static size_t set_to[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64)
+        return e != cudaSuccess ? e : cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (bytes <= set_to[dev])
+        return cudaSuccess;
+    e = cudaFuncSetAttribute(monopole_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        set_to[dev] = bytes;
+    return e;
+}
+
+extern "C" oct_status oct_hydro_gravity_monopole(oct_hydro_t h, const double *U, double G, double r_s, double *phi,
+                                                 double *g, void *cuda_stream)
+{
+    DeviceGuard device_guard(h);
+    NvtxRange nvtx_range("oct_hydro_gravity_monopole");
+    oct_status st = check_ready(h);
+    if (st != OCT_OK)
+        return st;
+    if ((st = check_ptr(U, "U")) != OCT_OK || (st = check_ptr(phi, "phi")) != OCT_OK ||
+        (st = check_ptr(g, "g")) != OCT_OK)
+        return st;
+    if (h->bc != OCT_BC_PERIODIC && h->bc != OCT_BC_OUTFLOW)
+        return fail(OCT_E_STATE, "gravity needs one level with a neighbour table (periodic or outflow layout)");
+    const int E = h->edge[0];
+    for (int s = 1; s < h->n_sub; s++)
+        if (h->dx[s] != h->dx[0])
+            return fail(OCT_E_ARG, "gravity needs one cell width for every subgrid (subgrid %d differs)", s);
+    if (!(G > 0.0) || !std::isfinite(G))
+        return fail(OCT_E_ARG, "G must be positive and finite (got %g)", G);
+    if (!(r_s >= 1.0) || !std::isfinite(r_s) || (int)std::floor(r_s) > E)
+        return fail(OCT_E_ARG, "r_s must be in [1, edge] cell widths (got %g)", r_s);
+    const int R = (int)std::floor(r_s);
+    const int S = E + 2 * R;
+    if (r_s != h->gst_rs || S != h->gst_S) {
+        // the stencil: offsets with 0 < |d|^2 <= r_s^2, z outermost, then y, then x
+        std::vector<int> off;
+        std::vector<GravEntry> k;
+        const double r2max = r_s * r_s;
+        for (int dz = -R; dz <= R; dz++)
+            for (int dy = -R; dy <= R; dy++)
+                for (int dxx = -R; dxx <= R; dxx++) {
+                    const double d2 = (double)(dxx * dxx + dy * dy + dz * dz);
+                    if (d2 == 0.0 || d2 > r2max)
+                        continue;
+                    const double r = std::sqrt(d2), r3 = d2 * r;
+                    off.push_back((dz * S + dy) * S + dxx);
+                    k.push_back(GravEntry{1.0 / r, dxx / r3, dy / r3, dz / r3});
+                }
+        dfree(h->d_gst_off);
+        dfree(h->d_gst_k);
+        h->gst_rs = 0.0;
+        CUDA_TRY(cudaMalloc(&h->d_gst_off, sizeof(int) * off.size()));
+        CUDA_TRY(cudaMalloc(&h->d_gst_k, sizeof(GravEntry) * k.size()));
+        CUDA_TRY(cudaMemcpy(h->d_gst_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(h->d_gst_k, k.data(), sizeof(GravEntry) * k.size(), cudaMemcpyHostToDevice));
+        h->gst_n = (int)off.size();
+        h->gst_rs = r_s;
+        h->gst_S = S;
+    }
+    const size_t smem = monopole_smem(S, h->gst_n);
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (smem > (size_t)optin)
+        return fail(OCT_E_ARG, "r_s = %g needs %zu bytes of shared memory for edge %d (at most %d)", r_s, smem, E,
+                    optin);
+    CUDA_TRY(monopole_smem_limit(smem));
+    const double dx = h->dx[0];
+    monopole_kernel<<<h->n_sub, MONO_THREADS, smem, (cudaStream_t)cuda_stream>>>(
+        U, h->d_off, E, h->d_nbr, R, h->gst_n, h->d_gst_off, h->d_gst_k, dx * dx * dx, -G / dx, G / (dx * dx), phi, g);
+    CUDA_TRY(cudaGetLastError());
+    return OCT_OK;
 }
 
 // ---------------------------------------------------------------------------

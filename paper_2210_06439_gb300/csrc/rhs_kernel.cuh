@@ -79,6 +79,14 @@ __device__ __forceinline__ bool mag_lt(int ah, unsigned int al, int bh, unsigned
     return ((unsigned int)ah < (unsigned int)bh) || (ah == bh && al < bl);
 }
 
+// Nonzero unless a and b have the same bit pattern (integer operations only).
+__device__ __forceinline__ unsigned bit_diff(double a, double b)
+{
+    const HL A = hl(a), B = hl(b);
+    return (unsigned)(A.h ^ B.h) | (A.l ^ B.l);
+}
+__device__ __forceinline__ unsigned bit_diff(float a, float b) { return __float_as_uint(a) ^ __float_as_uint(b); }
+
 // max of two non-negative (or NaN) doubles by their bit patterns
 __device__ __forceinline__ double max_nonneg(double x, double y)
 {
@@ -164,17 +172,32 @@ static __device__ __noinline__ void cw84_rare(double &d1, double &d2)
 // minus side and d2 becomes 2 d1; when |d1| > 2|d2|, d1 becomes 2 d2.
 // Finally up = u0 + d1, um = u0 - d2.  The FP64 operations run for every
 // lane; the constraints choose on the integer words.
-__device__ __forceinline__ void ppm5(double um2, double um1, double u0, double up1, double up2, double &vm,
+// Returns true when the stencil's five values are bitwise equal (the cell
+// value returned at both ends without arithmetic).
+__device__ __forceinline__ bool ppm5(double um2, double um1, double u0, double up1, double up2, double &vm,
                                      double &vp)
 {
+    // a stencil of five bitwise-equal values (uniform regions such as an
+    // atmosphere) is its own reconstruction: tested on the integer words
+    // before any FP64 operation, a branch so that warps with no other lanes
+    // skip the rest
+    {
+        const HL M2 = hl(um2), M1 = hl(um1), Z = hl(u0), Q1 = hl(up1), Q2 = hl(up2);
+        const unsigned d = (unsigned)((M2.h ^ Z.h) | (M1.h ^ Z.h) | (Q1.h ^ Z.h) | (Q2.h ^ Z.h)) |
+                           (M2.l ^ Z.l) | (M1.l ^ Z.l) | (Q1.l ^ Z.l) | (Q2.l ^ Z.l);
+        if (d == 0u) {
+            vm = u0;
+            vp = u0;
+            return true;
+        }
+    }
     const double am2 = um1 - um2, am1 = u0 - um1, ap1 = up1 - u0, ap2 = up2 - up1;
-    // a constant stencil (uniform regions such as an atmosphere) is its own
-    // reconstruction: a branch, so that warps with no other lanes skip the rest
+    // a constant stencil whose values differ only in the sign of zero
     const HL A2 = hl(am2), A1 = hl(am1), P1 = hl(ap1), P2 = hl(ap2);
     if (is_zero(A2) && is_zero(A1) && is_zero(P1) && is_zero(P2)) {
         vm = u0;
         vp = u0;
-        return;
+        return false;
     }
     const double dm = mc_slope(am2, am1);
     const double d0 = mc_slope(am1, ap1);
@@ -201,12 +224,21 @@ __device__ __forceinline__ void ppm5(double um2, double um1, double u0, double u
     // flat: both half-widths zero, so that up = um = u0
     vp = u0 + from_hl(flat ? 0 : D1.h, flat ? 0u : D1.l);
     vm = u0 - from_hl(flat ? 0 : D2.h, flat ? 0u : D2.l);
+    return false;
 }
 
 // The FP32 form: the interface values first, then the constraints on
 // d1 = up - u0 and d2 = u0 - um formed from them.
-__device__ __forceinline__ void ppm5(float um2, float um1, float u0, float up1, float up2, float &vm, float &vp)
+__device__ __forceinline__ bool ppm5(float um2, float um1, float u0, float up1, float up2, float &vm, float &vp)
 {
+    // five bitwise-equal values: the cell value at both ends (integer test)
+    const unsigned z = __float_as_uint(u0);
+    if (((__float_as_uint(um2) ^ z) | (__float_as_uint(um1) ^ z) | (__float_as_uint(up1) ^ z) |
+         (__float_as_uint(up2) ^ z)) == 0u) {
+        vm = u0;
+        vp = u0;
+        return true;
+    }
     const float am2 = um1 - um2, am1 = u0 - um1, ap1 = up1 - u0, ap2 = up2 - up1;
     const float dm = mc_slope(am2, am1);
     const float d0 = mc_slope(am1, ap1);
@@ -222,6 +254,7 @@ __device__ __forceinline__ void ppm5(float um2, float um1, float u0, float up1, 
     const float umc = fmaf(-2.f, d1, u0), upc = fmaf(2.f, d2, u0);
     vm = flat ? u0 : (A ? umc : um);
     vp = flat ? u0 : (Bp ? upc : up);
+    return false;
 }
 
 // Point primitives: velocity, pressure (dual energy) and sound speed.
@@ -297,7 +330,7 @@ __device__ __forceinline__ float sound_from_w(float rho, float p, float gamma, b
 // of txm x tym cells and nf fields.
 struct SmemPlan {
     int nc;          // cells per plane buffer row: interior + ring
-    size_t temp, saved, pr, prs, faccx, faccy, zacc, dxy, raw, red, lists, total;
+    size_t temp, saved, pr, prs, cpr, faccx, faccy, zacc, dxy, raw, red, lists, total;
 };
 
 __host__ __device__ inline SmemPlan smem_plan(int nf, int elem, bool staged, int txm, int tym)
@@ -312,6 +345,7 @@ __host__ __device__ inline SmemPlan smem_plan(int nf, int elem, bool staged, int
     const bool shared_prims = elem == 8;  // FP32 recomputes primitives per face point
     p.pr = shared_prims ? take((size_t)8 * 5 * p.nc * elem) : 0;
     p.prs = shared_prims ? take((size_t)9 * 5 * cin * elem) : 0;
+    p.cpr = shared_prims ? take((size_t)5 * p.nc * elem) : 0;
     p.faccx = take((size_t)nf * (txm + 1) * tym * elem);
     p.faccy = take((size_t)nf * txm * (tym + 1) * elem);
     p.zacc = take((size_t)2 * nf * cin * elem);
@@ -370,7 +404,7 @@ __device__ __forceinline__ void sfor(F &&f)
 // 64^3 box; two fields 0.78, four 0.82); the FP64 form keeps one field per
 // item (registers).
 template <class T, bool STAGED, int G, int NT>
-__device__ __forceinline__ void phase_a(T *temp, const float *raw, const double *Ub, long long FS, int B, int x0,
+__device__ __forceinline__ bool phase_a(T *temp, const float *raw, const double *Ub, long long FS, int B, int x0,
                                         int y0, int kz, bool inplane, int nf, int NC, int RWX, int plane,
                                         const int *lists, const int *nlist, const unsigned *magic, const int *so,
                                         int tid)
@@ -381,6 +415,7 @@ __device__ __forceinline__ void phase_a(T *temp, const float *raw, const double 
     // per line: its cell list (the x / y ring only for lines with a nonzero x /
     // y step, in planes that own x / y faces) and its item count; lines without
     // a z step have nothing to do in the boundary planes
+    bool sawc = false;  // a stencil of one value met
     int beg[NL + 1];
     beg[0] = 0;
     sfor<NL>([&](auto Lc) {
@@ -422,13 +457,14 @@ __device__ __forceinline__ void phase_a(T *temp, const float *raw, const double 
                             u[m + 2] = Num<T>::from_d(__ldg(ub + m * st));
                     }
                     T vm, vp;
-                    ppm5(u[0], u[1], u[2], u[3], u[4], vm, vp);
+                    sawc |= ppm5(u[0], u[1], u[2], u[3], u[4], vm, vp);
                     temp[((2 * L) * nf + f) * NC + ci] = vm;
                     temp[((2 * L + 1) * nf + f) * NC + ci] = vp;
                 }
             }
         });
     }
+    return sawc;
 }
 
 // PRIM: the state array holds the primitive variables w of every cell
@@ -444,6 +480,9 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
     // arithmetic is scarce); FP32: recomputed at each face point (cheap), which
     // saves a phase and its barrier per line group
     constexpr bool SHARED_PRIMS = sizeof(T) == 8;
+    // scale of the face sums: 1 in FP64, 1/36 in FP32 (exact Simpson weights)
+    constexpr double FSC = sizeof(T) == 8 ? 1.0 : 1.0 / 36.0;
+    constexpr double HWS = sizeof(T) == 8 ? 1.0 / 36.0 : 1.0;  // Simpson weight scale
     const int nf = A.nf;
     const SmemPlan P = smem_plan(nf, sizeof(T), STAGED, TXM, TYM);
     constexpr int NC = TXM * TYM + 2 * TXM + 2 * TYM;
@@ -456,6 +495,7 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
     T *saved = reinterpret_cast<T *>(smem + P.saved);  // [9][nf][64] +z ends of the previous plane
     T *pr = reinterpret_cast<T *>(smem + P.pr);        // [8 slots][5][NC] vx, vy, vz, p, c of the group
     T *prs = reinterpret_cast<T *>(smem + P.prs);      // [9][5][64] the same for the saved +z ends
+    T *cpr = reinterpret_cast<T *>(smem + P.cpr);      // [5][NC] the same of the plane's cells (c < 0: none)
     T *faccx = reinterpret_cast<T *>(smem + P.faccx);  // [nf][72]
     T *faccy = reinterpret_cast<T *>(smem + P.faccy);  // [nf][72]
     T *zacc = reinterpret_cast<T *>(smem + P.zacc);    // [2][nf][64]
@@ -483,6 +523,14 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
     // in execution order (largest first), so that CTAs which finish early take
     // the remaining items; without a ticket, a static round robin
     __shared__ int s_next;
+    // whether phase A of a line group met a stencil of one value (uniform
+    // data), by group parity: set in phase A, read after its barrier, cleared
+    // for the group after next during phase B2.  Only then do phases B1 and
+    // B2 look for uniform points and faces, so that data without uniform
+    // regions pays nothing for those tests
+    __shared__ int s_const[2];
+    if (tid < 2)
+        s_const[tid] = 0;
     for (int k = blockIdx.x; k < A.n_items;) {
         const int it = A.order != nullptr ? A.order[k] : k;
         const WorkItem W = A.items[it];
@@ -491,7 +539,7 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
         const long long FS = (long long)B * B * B;
         const double *Ub = A.U + A.off[s];
         double *dUb = A.dUdt + A.doff[s];
-        const double rdx = 1.0 / A.dx[s];
+        const double rdx = (1.0 / A.dx[s]) * FSC;  // FP32 face sums carry a factor 36
         const unsigned m_tx = rcp_div(tx), m_tx1 = rcp_div(tx + 1), m_ty = rcp_div(ty);
         const int rows_s = ty + 2 * NG, cols_s = tx + 2 * NG;  // staged plane of this item
         const unsigned m_rc = rcp_div(rows_s * cols_s), m_cols = rcp_div(cols_s);
@@ -550,12 +598,95 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
         for (int t = 0; t < 4; t++)
             magic[t] = rcp_div(nlist[t]);
 
+        // ---- uniform column: when every value the item reads -- the tile
+        // and its 3-cell halo over the planes -3 .. E+2, every field -- is one
+        // value per field, every face flux of the column is the same, so each
+        // cell's RHS is -(0 + 0) / dx = -0.0 exactly as the full path writes
+        // it, and a_max is max_k |v_k| + c of that state (the same primitive
+        // function as at the face points).  Both are written directly.  The
+        // test reads the column in rounds of NT values and leaves at the
+        // first round that finds a difference.  (Not with primitive
+        // reconstruction, or when boundary face fluxes are wanted.) ----
+        bool ucol = false;
+        if constexpr (!PRIM) {
+            if (A.faces == nullptr) {
+                const int cols = tx + 2 * NG, rows = ty + 2 * NG, planes = E + 2 * NG;
+                const double *ub0 = Ub + (long long)y0 * B + x0;  // ghosted (x0, y0, 0)
+                constexpr int VPT = 4;  // loads in flight per thread per round
+                int diff = 0;
+                if (cols == B) {
+                    // full-width tiles: each (field, plane) is one run of rows * B doubles,
+                    // 16-byte aligned (blocks start on 32 bytes; B = 14, 18 or 22 is even
+                    // and so is every row offset), read as double2
+                    const int run = rows * B / 2, n = nf * planes * run;
+                    const unsigned m_run = rcp_div(run), m_pl = rcp_div(planes);
+                    for (int r0 = 0; r0 < n && !diff; r0 += VPT * NT) {
+#pragma unroll
+                        for (int u = 0; u < VPT; u++) {
+                            const int q = r0 + u * NT + tid;
+                            if (q < n) {
+                                const int fz = div_by(q, m_run), v = q - fz * run;
+                                const int f = div_by(fz, m_pl), z = fz - f * planes;
+                                const double *fb = ub0 + f * FS;
+                                const double2 w =
+                                    __ldg(reinterpret_cast<const double2 *>(fb + (long long)z * B * B) + v);
+                                const double ref = __ldg(fb);
+                                diff |= (bit_diff(w.x, ref) | bit_diff(w.y, ref)) != 0u;
+                            }
+                        }
+                        diff = __syncthreads_or(diff);
+                    }
+                } else {
+                    const int per_f = planes * rows * cols, n = nf * per_f;
+                    const unsigned m_pf = rcp_div(per_f), m_rcs = rcp_div(rows * cols), m_cols = rcp_div(cols);
+                    for (int r0 = 0; r0 < n && !diff; r0 += VPT * NT) {
+#pragma unroll
+                        for (int u = 0; u < VPT; u++) {
+                            const int q = r0 + u * NT + tid;
+                            if (q < n) {
+                                const int f = div_by(q, m_pf), r = q - f * per_f;
+                                const int z = div_by(r, m_rcs), r2 = r - z * rows * cols;
+                                const int y = div_by(r2, m_cols), x = r2 - y * cols;
+                                const double v =
+                                    __ldg(ub0 + f * FS + (long long)z * B * B + (long long)y * B + x);
+                                diff |= bit_diff(v, __ldg(ub0 + f * FS)) != 0u;
+                            }
+                        }
+                        diff = __syncthreads_or(diff);
+                    }
+                }
+                ucol = !diff;
+                if (ucol) {
+                    T qh[6], v[3], p, c;
+#pragma unroll
+                    for (int f = 0; f < 6; f++)
+                        qh[f] = Num<T>::from_d(__ldg(ub0 + f * FS));
+                    prim_point(qh, gamma, gm1, ggm1, eps1, v, p, c, bad);
+                    const T a = max_nonneg(max_nonneg(fabs(v[0]) + c, fabs(v[1]) + c), fabs(v[2]) + c);
+                    amax = Num<T>::to_d(a);
+                    const int per = E * ty * tx;
+                    const unsigned m_per = rcp_div(per), m_tyx = rcp_div(ty * tx);
+                    for (int q = tid; q < nf * per; q += NT) {
+                        const int f = div_by(q, m_per), r = q - f * per;
+                        const int z = div_by(r, m_tyx), r2 = r - z * ty * tx;
+                        const int j = div_by(r2, m_tx), i = r2 - j * tx;
+                        dUb[(long long)f * E * E * E + (long long)z * E * E + (long long)(y0 + j) * E + (x0 + i)] = -0.0;
+                    }
+                }
+            }
+        }
+        if (!ucol) {
         for (int kz = -3; kz <= 1; kz++)
             stage_plane(kz);
         __syncthreads();
 
+        // the plane's cell primitives (FP64) are computed when the previous
+        // plane met uniform data (and for the first plane of an item)
+        bool cell_prev = true;
         for (int kz = -1; kz <= E; kz++) {
             const bool inplane = (kz >= 0 && kz < E);
+            const bool cells_ready = cell_prev;
+            bool plane_const = false;
             int so[5];  // staged-ring offsets of planes kz-2 .. kz+2
 #pragma unroll
             for (int m = 0; m < 5; m++)
@@ -575,11 +706,12 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                 const int n0 = nlist[t0], n1 = nl > 1 ? nlist[t1] : 0, n2 = nl > 2 ? nlist[t2] : 0,
                           n3 = nl > 3 ? nlist[t3] : 0;
                 // ---- phase A: 1-D PPM for every (line, field, cell) of the group ----
+                bool sawc = false;
                 switch (g) {
 #define OCT_PHASE_A(GG)                                                                                              \
     case GG:                                                                                                         \
-        phase_a<T, STAGED, GG, NT>(temp, raw, Ub, FS, B, x0, y0, kz, inplane, nf, NC, RWX, RWY * RWX, lists, nlist,     \
-                               magic, so, tid);                                                                      \
+        sawc = phase_a<T, STAGED, GG, NT>(temp, raw, Ub, FS, B, x0, y0, kz, inplane, nf, NC, RWX, RWY * RWX, lists,     \
+                                          nlist, magic, so, tid);                                                    \
         break;
                     OCT_PHASE_A(0)
                     OCT_PHASE_A(1)
@@ -587,7 +719,38 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                     OCT_PHASE_A(3)
 #undef OCT_PHASE_A
                 }
+                if constexpr (SHARED_PRIMS && !PRIM) {
+                    // primitives of the plane's cells themselves (interior and both
+                    // rings), once per plane: a point that carries its cell's values
+                    // takes them in phase B1 instead of computing its own.  A cell
+                    // whose primitives are not physical gets c = -1 (no point takes
+                    // them; its points are computed, and flagged, as usual)
+                    if (g == 0 && cells_ready) {
+                        const int t = inplane ? 3 : 0;
+                        for (int q = tid; q < nlist[t]; q += NT) {
+                            const int info = lists[t * NC + q];
+                            const int i = (info & 0xFF) - 1, j = ((info >> 8) & 0xFF) - 1, ci = info >> 16;
+                            const double *ub =
+                                Ub + (long long)(kz + NG) * B * B + (long long)(y0 + j + NG) * B + (x0 + i + NG);
+                            T qh[6], v[3], p, cs;
+#pragma unroll
+                            for (int f = 0; f < 6; f++)
+                                qh[f] = __ldg(ub + f * FS);
+                            bool cbad = false;
+                            prim_point(qh, gamma, gm1, ggm1, eps1, v, p, cs, cbad);
+                            cpr[ci] = v[0];
+                            cpr[NC + ci] = v[1];
+                            cpr[2 * NC + ci] = v[2];
+                            cpr[3 * NC + ci] = p;
+                            cpr[4 * NC + ci] = cbad ? T(-1) : cs;
+                        }
+                    }
+                }
+                if (sawc)
+                    s_const[g & 1] = 1;
                 __syncthreads();
+                const bool gconst = s_const[g & 1] != 0;
+                plane_const = plane_const || gconst;
                 if constexpr (SHARED_PRIMS) {
                 // ---- phase B1: primitives of every needed point of the group:
                 // both ends of interior cells (one end in the boundary planes),
@@ -664,7 +827,26 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
 #pragma unroll
                             for (int f = 0; f < 6; f++)
                                 qh[f] = temp[(slot * nf + f) * NC + ci];
-                            prim_point(qh, gamma, gm1, ggm1, eps1, v, p, cs, bad);
+                            // both ends of the line bitwise equal in every hydro field:
+                            // then both carry the cell's own values (PPM leaves a value
+                            // unchanged only by returning the cell value), and the
+                            // point's primitives are the cell's
+                            unsigned d = 1u;
+                            if (gconst && cells_ready) {
+                                d = 0u;
+#pragma unroll
+                                for (int f = 0; f < 6; f++)
+                                    d |= bit_diff(qh[f], temp[((slot ^ 1) * nf + f) * NC + ci]);
+                            }
+                            if (d == 0u && __double2hiint(cpr[4 * NC + ci]) >= 0) {
+                                v[0] = cpr[ci];
+                                v[1] = cpr[NC + ci];
+                                v[2] = cpr[2 * NC + ci];
+                                p = cpr[3 * NC + ci];
+                                cs = cpr[4 * NC + ci];
+                            } else {
+                                prim_point(qh, gamma, gm1, ggm1, eps1, v, p, cs, bad);
+                            }
                         }
                         T *o = pr + slot * 5 * NC + ci;
                         o[0] = v[0];
@@ -679,6 +861,8 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                 // ---- phase B2: KT flux at the group's points, one thread per face;
                 // the faces of the group's axes packed densely, each looping over
                 // its axis's points of the group ----
+                if (tid == 0)
+                    s_const[(g + 1) & 1] = 0;  // for the next group (read before two barriers ago)
                 {
                     const int nfx = (inplane && G.has[0]) ? (tx + 1) * ty : 0;
                     const int nfy = (inplane && G.has[1]) ? tx * (ty + 1) : 0;
@@ -708,10 +892,73 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                             acc[f] = T(0);
                         T pacc = T(0);
                         const int npa = axis == 0 ? G.nax[0] : (axis == 1 ? G.nax[1] : G.nax[2]);
-                        for (int k = 0; k < npa; k++) {
+                        // When every point of this face in the group carries one state u
+                        // on both sides (a uniform region), each point's KT flux is the
+                        // physical one, (v_L + a) u / 2 + (v_R - a) u / 2 = v u, and the
+                        // group's contribution is v u times its weight sum: the same sum
+                        // up to rounding, for a few operations (and, in FP32, one
+                        // primitive recovery instead of two per point).  Decided on the
+                        // integer words (every field, both sides, every point)
+                        bool uni = false;
+                        if constexpr (!PRIM) {
+                            const int p0 = G.apt[axis][0], l0 = G.lslot[p0];
+                            const T *q0 = l0 >= 16 ? saved + (l0 - 16) * nf * C64 + cl : temp + l0 * nf * NC + cl;
+                            const int s0 = l0 >= 16 ? C64 : NC;
+                            // the density of every point first (it differs first in
+                            // non-uniform data), then all other fields at once.  The
+                            // decision rests on the face's own point values only, which
+                            // every tile that computes this face forms bitwise alike, so
+                            // all of them take the same path and the flux of a face shared
+                            // by two tiles is one value (conservation)
+                            unsigned d = 0u;
+                            for (int pass = 0; pass < 2 && d == 0u; pass++) {
+                                const int f0 = pass == 0 ? 0 : 1, f1 = pass == 0 ? 1 : nf;
+                                for (int k = 0; k < npa; k++) {
+                                    const int pt = G.apt[axis][k], ls = G.lslot[pt], rs = G.rslot[pt];
+                                    const T *qL =
+                                        ls >= 16 ? saved + (ls - 16) * nf * C64 + cl : temp + ls * nf * NC + cl;
+                                    const int sL = ls >= 16 ? C64 : NC;
+                                    const T *qR = temp + rs * nf * NC + cr;
+                                    for (int f = f0; f < f1; f++) {
+                                        const T z = q0[f * s0];
+                                        d |= bit_diff(qL[f * sL], z) | bit_diff(qR[f * NC], z);
+                                    }
+                                }
+                            }
+                            uni = d == 0u;
+                            if (uni) {
+                                T v, pv, c;
+                                if constexpr (SHARED_PRIMS) {
+                                    const T *pp = l0 >= 16 ? prs + (l0 - 16) * 5 * C64 + cl : pr + l0 * 5 * NC + cl;
+                                    v = pp[axis * s0], pv = pp[3 * s0], c = pp[4 * s0];
+                                } else {
+                                    T qh[6], vv[3];
+#pragma unroll
+                                    for (int f = 0; f < 6; f++)
+                                        qh[f] = q0[f * s0];
+                                    prim_point(qh, gamma, gm1, ggm1, eps1, vv, pv, c, bad);
+                                    v = axis == 0 ? vv[0] : (axis == 1 ? vv[1] : vv[2]);
+                                }
+                                const T a = fabs(v) + c;
+                                amax = max_nonneg(amax, Num<T>::to_d(a));
+                                const T W = SHARED_PRIMS ? T(axis == 0 ? G.wsum[0] : (axis == 1 ? G.wsum[1] : G.wsum[2]))
+                                                         : T(axis == 0 ? G.wnum[0] : (axis == 1 ? G.wnum[1] : G.wnum[2]));
+                                const T vw2 = (v + v) * W, pw2 = (pv + pv) * W;
+#pragma unroll
+                                for (int f = 0; f < MAXNF; f++)
+                                    if (f < nf)
+                                        acc[f] = vw2 * q0[f * s0];
+                                pacc = pw2;
+                                acc[F_EGAS] = fma(pw2, v, acc[F_EGAS]);
+                            }
+                        }
+                        for (int k = 0; k < (uni ? 0 : npa); k++) {
                             const int pt = G.apt[axis][k];
                             // half the Simpson weight (16, 4 or 1)/36
-                            const T hw = G.wcls[pt] == 0 ? T(8.0 / 36.0) : (G.wcls[pt] == 1 ? T(2.0 / 36.0) : T(0.5 / 36.0));
+                            // FP64: half the Simpson weight (16, 4 or 1)/36; FP32: 36 times
+                            // that (8, 2 or 1/2, exact), the factor 1/36 applied in FP64
+                            // after the face sum is promoted
+                            const T hw = G.wcls[pt] == 0 ? T(8.0 * HWS) : (G.wcls[pt] == 1 ? T(2.0 * HWS) : T(0.5 * HWS));
                             const int ls = G.lslot[pt], rs = G.rslot[pt];
                             const T *qL, *pL_;
                             int sL;
@@ -754,11 +1001,23 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                             }
                             const T a = max_nonneg(fabs(vkL) + cL, fabs(vkR) + cR);
                             amax = max_nonneg(amax, Num<T>::to_d(a));
-                            // F_f = (F_f(L) + F_f(R))/2 - a (u_R - u_L)/2 written per side:
-                            // alpha u_L + beta u_R, alpha = (v_L + a)/2, beta = (v_R - a)/2,
-                            // plus the pressure terms of the normal momentum and the energy
+                            // F_f = (F_f(L) + F_f(R))/2 - a (u_R - u_L)/2, plus the pressure
+                            // terms of the normal momentum and the energy.  FP64: written per
+                            // side, alpha u_L + beta u_R with alpha = (v_L + a)/2, beta =
+                            // (v_R - a)/2 (two FMAs a field).  FP32: as alpha (u_L - u_R) +
+                            // (alpha + beta) u_R, alpha + beta = (v_L + v_R)/2, whose rounding
+                            // scales with the flux v u and the jump a (u_L - u_R) rather than
+                            // with a u (a > |v| in subsonic flow, where the two per-side terms
+                            // nearly cancel)
                             const T al = (vkL + a) * hw;
                             const T be = (vkR - a) * hw;
+                            const T ab = (vkL + vkR) * hw;  // alpha + beta
+                            auto kt = [&](T uL, T uR, T accf) -> T {
+                                if constexpr (sizeof(T) == 8)
+                                    return fma(al, uL, fma(be, uR, accf));
+                                else
+                                    return fma(al, uL - uR, fma(ab, uR, accf));
+                            };
                             if constexpr (PRIM && !SHARED_PRIMS) {
                                 // conserved fields of both sides from w, field by field
                                 const T rL = qL[0], rR = qR[0];
@@ -778,17 +1037,20 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                                         } else {  // momenta and species: rho times v or X
                                             uL = rL * qL[f * sL], uR = rR * qR[f * NC];
                                         }
-                                        acc[f] = fma(al, uL, fma(be, uR, acc[f]));
+                                        acc[f] = kt(uL, uR, acc[f]);
                                     }
                             } else {
 #pragma unroll
                                 for (int f = 0; f < MAXNF; f++)
                                     if (f < nf)
-                                        acc[f] = fma(al, qL[f * sL], fma(be, qR[f * NC], acc[f]));
+                                        acc[f] = kt(qL[f * sL], qR[f * NC], acc[f]);
                             }
                             // pressure terms: the normal momentum's once per face (below),
                             // the energy's p v_k per point
-                            pacc = fma(pLv + pRv, hw, pacc);
+                            if constexpr (sizeof(T) == 8)
+                                pacc = fma(pLv + pRv, hw, pacc);
+                            else
+                                pacc = fma(pLv, hw, fma(pRv, hw, pacc));  // exact products (hw = 2^k)
                             acc[F_EGAS] = fma(fma(pLv, vkL, pRv * vkR), hw, acc[F_EGAS]);
                         }
 #pragma unroll
@@ -852,7 +1114,7 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                     for (int q = tid; q < nf * ncin; q += NT) {
                         int f = div_by(q, magic[0]), c = q - f * ncin;
                         int j = div_by(c, m_tx), i = c - j * tx;
-                        o[(long long)f * E * E + (y0 + j) * E + (x0 + i)] = Num<T>::to_d(zs[f * C64 + c]);
+                        o[(long long)f * E * E + (y0 + j) * E + (x0 + i)] = Num<T>::to_d(zs[f * C64 + c]) * FSC;
                     }
                 }
                 if (inplane && A.faces != nullptr && (x0 == 0 || y0 == 0 || x0 + tx == E || y0 + ty == E) &&
@@ -865,9 +1127,9 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                             const T *fx = faccx + f * FXS + j * (tx + 1);
                             const long long o = f * EE + (long long)kz * E + (y0 + j);
                             if (x0 == 0)
-                                fb[o] = Num<T>::to_d(fx[0]);
+                                fb[o] = Num<T>::to_d(fx[0]) * FSC;
                             if (x0 + tx == E)
-                                fb[nf * EE + o] = Num<T>::to_d(fx[tx]);
+                                fb[nf * EE + o] = Num<T>::to_d(fx[tx]) * FSC;
                         }
                     if (y0 == 0 || y0 + ty == E)
                         for (int q = tid; q < nf * tx; q += NT) {
@@ -875,9 +1137,9 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                             const T *fy = faccy + f * FYS;
                             const long long o = f * EE + (long long)kz * E + (x0 + i);
                             if (y0 == 0)
-                                fb[2 * nf * EE + o] = Num<T>::to_d(fy[i]);
+                                fb[2 * nf * EE + o] = Num<T>::to_d(fy[i]) * FSC;
                             if (y0 + ty == E)
-                                fb[3 * nf * EE + o] = Num<T>::to_d(fy[ty * tx + i]);
+                                fb[3 * nf * EE + o] = Num<T>::to_d(fy[ty * tx + i]) * FSC;
                         }
                 }
             }
@@ -889,7 +1151,9 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
             // z-face slot read above) comes after two more barriers
             if constexpr (STAGED)
                 __syncthreads();
+            cell_prev = plane_const;
         }
+        }  // !ucol
         // ---- max signal speed of this item ----
         for (int o = 16; o > 0; o >>= 1)
             amax = fmax(amax, __shfl_xor_sync(0xFFFFFFFFu, amax, o));

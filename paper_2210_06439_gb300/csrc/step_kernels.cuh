@@ -65,36 +65,25 @@ struct CombineArgs {
     unsigned *flags;
 };
 
-// One SSP-RK3 combine (Shu-Osher) on the interior, one thread per interior
-// cell of the whole batch (cell q of subgrid s at q - cell_begin[s]):
+// One SSP-RK3 combine (Shu-Osher) on the interior:
 //   stage 1: out = X + dt L                     (X = U0)
 //   stage 2: out = 3/4 U0 + 1/4 (X + dt L)
 //   stage 3: out = 1/3 U0 + 2/3 (X + dt L)
 // then the floors rho >= rho_floor, rho_i >= 0, the tau re-synchronisation
 // tau = e_int^(1/gamma) where e_int = E - |s|^2/(2 rho) > eps2 E, and tau >= 0.
-// All loads of a cell are issued before its stores.
+// `parts` blocks per subgrid (block b works on subgrid b / parts), each
+// thread on interior cells c = part * blockDim + threadIdx, c + parts *
+// blockDim, ... (x fastest, so a warp reads whole interior rows); all loads
+// of a cell are issued before its stores.
 // Three CTAs per SM (80 registers): the kernel waits on memory, and 24 warps
 // per SM hide more of it than the 16 that 103 registers allowed.
-__global__ void __launch_bounds__(256, 3)
-    combine_kernel(CombineArgs A, int n_sub, const long long *cell_begin, long long n_cells)
+__global__ void __launch_bounds__(256, 3) combine_kernel(CombineArgs A, int parts)
 {
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n_cells)
-        return;
-    // subgrid of this cell: binary search over the packed cell offsets
-    int lo = 0, hi = n_sub - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (cell_begin[mid] <= q)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const int s = lo;
+    const int s = blockIdx.x / parts, part = blockIdx.x - s * parts;
     const int E = A.edge[s], B = E + 2 * NG;
     const long long FS = (long long)B * B * B;
-    const long long E3 = (long long)E * E * E;
-    const int c = (int)(q - cell_begin[s]);
+    const int E3 = E * E * E;
+    const long long gbase = A.off[s], lbase = A.doff[s];
     const double dt = A.dt[0];
     double a, b;
     if (A.stage == 1) {
@@ -107,54 +96,56 @@ __global__ void __launch_bounds__(256, 3)
         a = 1.0 / 3.0;
         b = 2.0 / 3.0;
     }
-    const unsigned m_E = E == 8 ? rcp_div(8) : (E == 12 ? rcp_div(12) : rcp_div(16));
-    const int zy = div_by(c, m_E), z = div_by(zy, m_E);
-    const int x = c - zy * E, y = zy - z * E;
-    const long long gi = A.off[s] + ((long long)(z + NG) * B + (y + NG)) * B + (x + NG);
-    const long long li = A.doff[s] + c;
-    double xv[MAXNF], lv[MAXNF], u0[MAXNF];
+    const unsigned m_E = rcp_div(E);
+    for (int c = part * blockDim.x + threadIdx.x; c < E3; c += parts * blockDim.x) {
+        const int zy = div_by(c, m_E), z = div_by(zy, m_E);
+        const int x = c - zy * E, y = zy - z * E;
+        const long long gi = gbase + ((long long)(z + NG) * B + (y + NG)) * B + (x + NG);
+        const long long li = lbase + c;
+        double xv[MAXNF], lv[MAXNF], u0[MAXNF];
 #pragma unroll
-    for (int f = 0; f < MAXNF; f++)
-        if (f < A.nf) {
-            xv[f] = A.X[gi + f * FS];
-            lv[f] = A.L[li + f * E3];
-            u0[f] = A.stage == 1 ? 0.0 : A.U0[gi + f * FS];
-        }
-    double u[MAXNF];
-#pragma unroll
-    for (int f = 0; f < MAXNF; f++)
-        if (f < A.nf) {
-            const double x1 = xv[f] + dt * lv[f];
-            u[f] = (A.stage == 1) ? x1 : a * u0[f] + b * x1;
-        }
-    bool fired = false;
-    if (u[F_RHO] < A.rho_floor) {
-        u[F_RHO] = A.rho_floor;
-        fired = true;
-    }
-#pragma unroll
-    for (int f = F_SPC; f < MAXNF; f++)
-        if (f < A.nf) {
-            const int hi = __double2hiint(u[f]);
-            if (hi < 0 && ((hi & 0x7FFFFFFF) | __double2loint(u[f])) != 0) {  // negative, not -0
-                u[f] = 0.0;
-                fired = true;
+        for (int f = 0; f < MAXNF; f++)
+            if (f < A.nf) {
+                xv[f] = A.X[gi + f * FS];
+                lv[f] = A.L[li + f * E3];
+                u0[f] = A.stage == 1 ? 0.0 : A.U0[gi + f * FS];
             }
-        }
-    const double ei =
-        u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) * rcp_nr(u[F_RHO]);
-    if (ei > A.eps2 * u[F_EGAS])
-        u[F_TAU] = tau_of_eint(ei, A.gamma);
-    if (u[F_TAU] < 0.0) {
-        u[F_TAU] = 0.0;
-        fired = true;
-    }
+        double u[MAXNF];
 #pragma unroll
-    for (int f = 0; f < MAXNF; f++)
-        if (f < A.nf)
-            A.out[gi + f * FS] = u[f];
-    if (fired)
-        atomicOr(A.flags, 2u);
+        for (int f = 0; f < MAXNF; f++)
+            if (f < A.nf) {
+                const double x1 = xv[f] + dt * lv[f];
+                u[f] = (A.stage == 1) ? x1 : a * u0[f] + b * x1;
+            }
+        bool fired = false;
+        if (u[F_RHO] < A.rho_floor) {
+            u[F_RHO] = A.rho_floor;
+            fired = true;
+        }
+#pragma unroll
+        for (int f = F_SPC; f < MAXNF; f++)
+            if (f < A.nf) {
+                const int hi = __double2hiint(u[f]);
+                if (hi < 0 && ((hi & 0x7FFFFFFF) | __double2loint(u[f])) != 0) {  // negative, not -0
+                    u[f] = 0.0;
+                    fired = true;
+                }
+            }
+        const double ei =
+            u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) * rcp_nr(u[F_RHO]);
+        if (ei > A.eps2 * u[F_EGAS])
+            u[F_TAU] = tau_of_eint(ei, A.gamma);
+        if (u[F_TAU] < 0.0) {
+            u[F_TAU] = 0.0;
+            fired = true;
+        }
+#pragma unroll
+        for (int f = 0; f < MAXNF; f++)
+            if (f < A.nf)
+                A.out[gi + f * FS] = u[f];
+        if (fired)
+            atomicOr(A.flags, 2u);
+    }
 }
 
 // The ghost shell of a subgrid of edge E, enumerated as: the two z slabs

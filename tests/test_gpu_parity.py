@@ -277,3 +277,64 @@ def test_dual_energy_switch_over_wide_tau_range(recon):
         assert np.all(errs <= 1e-12), (s, shifts[s], errs)
         o += nf * E3
     np.testing.assert_allclose(am.cpu().numpy(), am_o, rtol=1e-12)
+
+
+def _halo_case(case):
+    """A uniform state with values changed in one subgrid's block only: a
+    ramp of every field across the three ghost layers below x (two rows),
+    below z or above y, tau alone in the interior, a species alone in the
+    interior, or the block's far corner (read by no stencil).  Returns the
+    problem and the changed fields."""
+    p = oracle_filled(inputs.uniform_state(nsub=(2, 2, 1), v=(0.3, -0.2, 0.1), n_species=5))
+    blk = p.block(1)
+    e = 0.3
+    fields = list(range(p.nf))
+    if case == "x_ramp":
+        for k in range(3):
+            blk[:, 3, 3:5, k] *= 1 + e * (3 - k)
+    elif case == "z_ramp":
+        for k in range(3):
+            blk[:, k, 5, 6] *= 1 + e * (3 - k)
+    elif case == "y_ramp":
+        for k in range(3):
+            blk[:, 6, 13 - k, 4] *= 1 + e * (3 - k)
+    elif case == "interior_tau":
+        blk[5, 7, 6, 5] *= 1 + e
+        fields = [5]
+    elif case == "interior_species":
+        blk[7, 7, 7, 7] *= 1 + e
+        fields = [7]
+    else:
+        blk[:, 0, 0, 0] *= 1 + e
+        fields = []
+    return p, fields
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", ["x_ramp", "z_ramp", "y_ramp", "interior_tau", "interior_species", "corner"])
+def test_uniform_column_test_sees_every_value_read(case, precision):
+    """Work items whose column (the tile, its 3-cell halo, every field) holds
+    one value per field write their RHS and signal speed without the
+    reconstruction.  Here one subgrid's block is uniform but for a few
+    values in its halo or interior: the items that read them must take the
+    full path.  The changed fields match the oracle at the form's tolerance;
+    the others (exactly zero in the oracle where only one field changed)
+    stay within that tolerance of the changed fields' scale; the corner,
+    read by no stencil, leaves the RHS exactly zero."""
+    p, fields = _halo_case(case)
+    d_o, am_o, nb = oracle.rhs(p.edge, p.off, p.dx, p.nf, p.U)
+    assert nb == 0
+    d_g, am_g, flags, _, _ = _gpu_rhs(p, precision, fill=False)
+    assert flags == 0
+    np.testing.assert_allclose(am_g, am_o, rtol=1e-12 if precision == 0 else MIXED_SPEED_RTOL)
+    if not fields:
+        assert not np.any(d_o) and not np.any(d_g)
+        return
+    errs = field_errors(d_g, d_o, p.nf, e3s(p))
+    assert np.all(errs[fields] <= TOL[precision]), errs
+    G = d_g.reshape(p.n_sub, p.nf, -1)
+    O = d_o.reshape(p.n_sub, p.nf, -1)
+    scale = max(float(np.max(np.abs(O[:, f]))) for f in fields)
+    assert scale > 0
+    for f in range(p.nf):
+        assert np.max(np.abs(G[:, f] - O[:, f])) <= TOL[precision] * scale, f
