@@ -39,8 +39,6 @@ struct GroupTab {
     int napt;                      // face points per face, the most over the axes
     int nax[3];                    // face points per face of each axis
     signed char apt[3][4];         // indices into the point arrays, per face axis
-    double wsum[3];                // sum of the half Simpson weights of each axis's points
-    float wnum[3];                 // the same times 36 (sums of 8, 2 and 1/2: exact)
 };
 constexpr int NGROUPS = 4;
 

@@ -67,18 +67,8 @@ bool build_group_tables(GroupTab *gs)
             G.apt[k][cnt[k]++] = (signed char)p;
         }
         G.napt = cnt[0] > cnt[1] ? (cnt[0] > cnt[2] ? cnt[0] : cnt[2]) : (cnt[1] > cnt[2] ? cnt[1] : cnt[2]);
-        for (int k = 0; k < 3; k++) {
+        for (int k = 0; k < 3; k++)
             G.nax[k] = cnt[k];
-            // half the Simpson weights (16, 4, 1)/36 of the axis's points: their
-            // numerators (exact) summed, then one division
-            double num = 0.0;
-            for (int q = 0; q < cnt[k]; q++) {
-                const int w = G.wcls[G.apt[k][q]];
-                num += w == 0 ? 8.0 : (w == 1 ? 2.0 : 0.5);
-            }
-            G.wsum[k] = num / 36.0;
-            G.wnum[k] = (float)num;
-        }
         for (int l = 0; l < G.nl; l++) {
             if (!G.line[l][2])
                 continue;

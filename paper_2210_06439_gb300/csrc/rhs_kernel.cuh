@@ -229,16 +229,12 @@ __device__ __forceinline__ bool ppm5(double um2, double um1, double u0, double u
 
 // The FP32 form: the interface values first, then the constraints on
 // d1 = up - u0 and d2 = u0 - um formed from them.
+// No test for stencils of one value here: a constant stencil already gives
+// u0 at both ends through the arithmetic below, the FP32 form has no phase B1
+// to feed, and whole uniform columns never reach this phase; on data without
+// uniform regions the test cost about 4% of the RHS.
 __device__ __forceinline__ bool ppm5(float um2, float um1, float u0, float up1, float up2, float &vm, float &vp)
 {
-    // five bitwise-equal values: the cell value at both ends (integer test)
-    const unsigned z = __float_as_uint(u0);
-    if (((__float_as_uint(um2) ^ z) | (__float_as_uint(um1) ^ z) | (__float_as_uint(up1) ^ z) |
-         (__float_as_uint(up2) ^ z)) == 0u) {
-        vm = u0;
-        vp = u0;
-        return true;
-    }
     const float am2 = um1 - um2, am1 = u0 - um1, ap1 = up1 - u0, ap2 = up2 - up1;
     const float dm = mc_slope(am2, am1);
     const float d0 = mc_slope(am1, ap1);
@@ -892,67 +888,7 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                             acc[f] = T(0);
                         T pacc = T(0);
                         const int npa = axis == 0 ? G.nax[0] : (axis == 1 ? G.nax[1] : G.nax[2]);
-                        // When every point of this face in the group carries one state u
-                        // on both sides (a uniform region), each point's KT flux is the
-                        // physical one, (v_L + a) u / 2 + (v_R - a) u / 2 = v u, and the
-                        // group's contribution is v u times its weight sum: the same sum
-                        // up to rounding, for a few operations (and, in FP32, one
-                        // primitive recovery instead of two per point).  Decided on the
-                        // integer words (every field, both sides, every point)
-                        bool uni = false;
-                        if constexpr (!PRIM) {
-                            const int p0 = G.apt[axis][0], l0 = G.lslot[p0];
-                            const T *q0 = l0 >= 16 ? saved + (l0 - 16) * nf * C64 + cl : temp + l0 * nf * NC + cl;
-                            const int s0 = l0 >= 16 ? C64 : NC;
-                            // the density of every point first (it differs first in
-                            // non-uniform data), then all other fields at once.  The
-                            // decision rests on the face's own point values only, which
-                            // every tile that computes this face forms bitwise alike, so
-                            // all of them take the same path and the flux of a face shared
-                            // by two tiles is one value (conservation)
-                            unsigned d = 0u;
-                            for (int pass = 0; pass < 2 && d == 0u; pass++) {
-                                const int f0 = pass == 0 ? 0 : 1, f1 = pass == 0 ? 1 : nf;
-                                for (int k = 0; k < npa; k++) {
-                                    const int pt = G.apt[axis][k], ls = G.lslot[pt], rs = G.rslot[pt];
-                                    const T *qL =
-                                        ls >= 16 ? saved + (ls - 16) * nf * C64 + cl : temp + ls * nf * NC + cl;
-                                    const int sL = ls >= 16 ? C64 : NC;
-                                    const T *qR = temp + rs * nf * NC + cr;
-                                    for (int f = f0; f < f1; f++) {
-                                        const T z = q0[f * s0];
-                                        d |= bit_diff(qL[f * sL], z) | bit_diff(qR[f * NC], z);
-                                    }
-                                }
-                            }
-                            uni = d == 0u;
-                            if (uni) {
-                                T v, pv, c;
-                                if constexpr (SHARED_PRIMS) {
-                                    const T *pp = l0 >= 16 ? prs + (l0 - 16) * 5 * C64 + cl : pr + l0 * 5 * NC + cl;
-                                    v = pp[axis * s0], pv = pp[3 * s0], c = pp[4 * s0];
-                                } else {
-                                    T qh[6], vv[3];
-#pragma unroll
-                                    for (int f = 0; f < 6; f++)
-                                        qh[f] = q0[f * s0];
-                                    prim_point(qh, gamma, gm1, ggm1, eps1, vv, pv, c, bad);
-                                    v = axis == 0 ? vv[0] : (axis == 1 ? vv[1] : vv[2]);
-                                }
-                                const T a = fabs(v) + c;
-                                amax = max_nonneg(amax, Num<T>::to_d(a));
-                                const T W = SHARED_PRIMS ? T(axis == 0 ? G.wsum[0] : (axis == 1 ? G.wsum[1] : G.wsum[2]))
-                                                         : T(axis == 0 ? G.wnum[0] : (axis == 1 ? G.wnum[1] : G.wnum[2]));
-                                const T vw2 = (v + v) * W, pw2 = (pv + pv) * W;
-#pragma unroll
-                                for (int f = 0; f < MAXNF; f++)
-                                    if (f < nf)
-                                        acc[f] = vw2 * q0[f * s0];
-                                pacc = pw2;
-                                acc[F_EGAS] = fma(pw2, v, acc[F_EGAS]);
-                            }
-                        }
-                        for (int k = 0; k < (uni ? 0 : npa); k++) {
+                        for (int k = 0; k < npa; k++) {
                             const int pt = G.apt[axis][k];
                             // half the Simpson weight (16, 4 or 1)/36
                             // FP64: half the Simpson weight (16, 4 or 1)/36; FP32: 36 times
@@ -1081,12 +1017,21 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                         }
                     }
                 }
+                if constexpr (STAGED) {
+                    // phase A of the last line group (every group has lines with a z
+                    // step, so it runs in every plane) was the last reader of plane
+                    // kz-2 in the FP32 ring: plane kz+3 is staged into its slot now,
+                    // while phase B2 occupies fewer than half the threads, and this
+                    // barrier completes it before the next plane's phase A
+                    if (g == NGROUPS - 1 && kz + 3 <= E + 2)
+                        stage_plane(kz + 3);
+                }
                 __syncthreads();
             }
             // ---- plane end, one pass: the divergence of plane kz-1 (its upper z
             // face is done) and the in-plane part of plane kz's, by the same
             // thread for each (field, cell), so dxy is read before it is
-            // rewritten; then the next plane is staged ----
+            // rewritten ----
             for (int q = tid; q < nf * ncin; q += NT) {
                 int f = div_by(q, magic[0]), c = q - f * ncin;
                 int j = div_by(c, m_tx), i = c - j * tx;
@@ -1143,14 +1088,9 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                         }
                 }
             }
-            if (kz + 3 <= E + 2)
-                stage_plane(kz + 3);
-            // the staged plane must be complete before the next phase A reads it;
-            // without staging nothing here is read by the next plane's phase A or
-            // phase B1, and its phase B2 (which rewrites the face sums and the
-            // z-face slot read above) comes after two more barriers
-            if constexpr (STAGED)
-                __syncthreads();
+            // nothing here is read by the next plane's phase A or phase B1, and
+            // its phase B2 (which rewrites the face sums and the z-face slot read
+            // above) comes after two more barriers
             cell_prev = plane_const;
         }
         }  // !ucol
