@@ -455,6 +455,10 @@ def run_ours(args, rank, world):
                                    "hbm_gbs": mx_gbs, "hbm_frac": mx_gbs / hbm_peak}},
         "roofline": {"bound": "alu", "achieved": rhs_tflops, "peak": f64_peak, "unit": "TFLOP/s",
                      "frac": rhs_tflops / f64_peak,
+                     # which roof the kernel is nearest on this workload: on the binary
+                     # star most subgrids take the uniform-column path, and the rest
+                     # runs below both roofs (barriers and memory latency)
+                     "limiter": bound_of(rhs_tflops / f64_peak, rhs_gbs / hbm_peak),
                      "traffic": RHS_FP64_TRAFFIC.get(args.workload) if args.recon == 0 else None,
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "kernel": "rhs_kernel<double> (FP64 RHS)",

@@ -338,3 +338,26 @@ def test_uniform_column_test_sees_every_value_read(case, precision):
     assert scale > 0
     for f in range(p.nf):
         assert np.max(np.abs(G[:, f] - O[:, f])) <= TOL[precision] * scale, f
+
+
+def test_host_buffer_calls_match_device_calls_bitwise():
+    """oct_hydro_rk_steps_host and oct_hydro_rhs_host on a pinned host state
+    of 124 MB give the same bits as oct_hydro_rk_step and oct_hydro_rhs on a
+    device copy of it."""
+    torch = _torch()
+    p = oracle_filled(inputs.periodic_box())
+    H = _hydro(p)
+    st = torch.cuda.Stream()
+    U = torch.from_numpy(p.U.copy()).cuda()
+    d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+    H.rhs(U, d, stream=st)
+    for _ in range(2):
+        H.rk_step(U, want_dt=False, stream=st)
+    torch.cuda.synchronize()
+    Uh = torch.from_numpy(p.U.copy()).pin_memory()
+    dh = torch.zeros(H.rhs_len, dtype=torch.float64).pin_memory()
+    H.rhs_host(Uh, dh, stream=st)
+    H.rk_steps_host(Uh, 2, stream=st)
+    assert torch.equal(dh, d.cpu())
+    assert torch.equal(Uh, U.cpu())
+    assert H.error_flags() == 0
