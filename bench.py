@@ -14,11 +14,12 @@ roofline divides by are measured in the same process.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME]
-  python bench.py --profile-rhs [--workload NAME] [--precision 0|1] [--reps R]
+  python bench.py --profile rhs|step|gravity [--workload NAME] [--precision 0|1] [--reps R]
 
 --impl reference times the FP64 CPU oracle (the reference arm) on the host
-cores for the same metric.  --profile-rhs only runs R RHS launches of one
-form on the workload (after one autotuning pass unless --no-autotune), for
+cores for the same metric.  --profile only runs R launches of one path on the
+workload (the RHS or the graph-replayed SSP-RK3 step of one form, after one
+autotuning pass unless --no-autotune, or the monopole gravity kernel), for
 captures under a profiler; it prints no benchmark line.
 """
 from __future__ import annotations
@@ -68,7 +69,8 @@ SHAPES = {
     "amr_box_64": (lambda: [8] * 568, 5),
 }
 UNIT = "cell-updates/s"
-STEP = "one step = one SSP-RK3 step (3 RHS + dt + 3 combine/floor + 3 ghost fill), FP64"
+STEP = ("one step = one SSP-RK3 step (3 RHS + dt + 3 combine/floor + 3 ghost fill), FP64, each timed step from "
+        "the initial state")
 
 # ---------------------------------------------------------------------------
 # Work and byte counts per cell: the floating-point arithmetic of the
@@ -326,16 +328,21 @@ def run_ours(args, rank, world):
         dU = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
         return H, U, dU
 
-    def timed(fn, k, w):
+    def timed(fn, k, w, reset=None):
         """Runs fn w times untimed, then k times each between its own events
-        (L2 flushed before each).  Returns per-iteration ms."""
+        (L2 flushed before each, and reset() run before that, outside the
+        events, when given).  Returns per-iteration ms."""
         for _ in range(w):
             with torch.cuda.stream(stream):
+                if reset is not None:
+                    reset()
                 fn()
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         for a, b in evs:
             with torch.cuda.stream(stream):
+                if reset is not None:
+                    reset()
                 flush.fill_(1.0)
                 a.record(stream)
                 fn()
@@ -349,24 +356,33 @@ def run_ours(args, rank, world):
         H, U, dU = make(prec)
         H.autotune(U, stream=stream)
         U0 = U.clone()
-        # full RK3 step (graph replay) -- the timed step
+        # full RK3 step (graph replay) -- the timed step; every timed step
+        # starts from the workload's initial state, restored before the L2
+        # flush outside the timed region, so that each measures the same work
+        # (the state evolves within a step and the cost of later steps
+        # depends on how many came before: reported apart as "evolving")
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         if prec == binding.OCT_FP64:
             sampler.start()
-        step_ms = timed(lambda: H.rk_step(U, want_dt=False, stream=stream), args.steps, args.warmup)
+        step_ms = timed(lambda: H.rk_step(U, want_dt=False, stream=stream), args.steps, args.warmup,
+                        reset=lambda: U.copy_(U0))
         if prec == binding.OCT_FP64:
             clocks = sampler.stop()
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
+        # K consecutive steps from the initial state, each timed
+        U.copy_(U0)
+        torch.cuda.synchronize()
+        evolve_ms = timed(lambda: H.rk_step(U, want_dt=False, stream=stream), args.steps, 0)
         # the RHS kernel alone (dominant kernel), same stream
         U.copy_(U0)
         rhs_ms = timed(lambda: H.rhs(U, dU, stream=stream), args.steps, args.warmup)
         flags = H.error_flags()
         results[prec] = dict(step_ms=step_ms, rhs_ms=rhs_ms, flags=flags, H=H, U=U, dU=dU, U0=U0,
-                             launch=H.launch_info())
+                             launch=H.launch_info(), evolve_ms=evolve_ms)
 
     # same-level monopole gravity (a separate solver step, not part of the
     # hydro RK3 step): its kernel alone, on the FP64 handle's state
@@ -385,14 +401,18 @@ def run_ours(args, rank, world):
     H64 = results[binding.OCT_FP64]["H"]
     Uh = torch.from_numpy(prob.U.copy()).pin_memory()
     H64.fill_ghosts(results[binding.OCT_FP64]["U"], stream=stream)
+    torch.cuda.synchronize()
     Uh.copy_(results[binding.OCT_FP64]["U"].cpu())
+    Uh0 = Uh.clone()  # each timed call starts from the initial state, like the device-timed steps
     H64.rk_steps_host(Uh, 1, stream=stream)
     torch.cuda.synchronize()
     e2e_ms = []
-    for _ in range(max(3, min(args.steps, 10))):
+    for _ in range(max(3, min(args.steps, 5))):
+        Uh.copy_(Uh0)
         t0 = time.perf_counter()
         H64.rk_steps_host(Uh, 1, stream=stream)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    del Uh0
 
     # reduce over ranks: max time
     s64 = results[binding.OCT_FP64]
@@ -445,6 +465,13 @@ def run_ours(args, rank, world):
         "data": "synthetic (seeded generators of paper_2210_06439_gb300.inputs)",
         "config": config,
         "rhs": {"value": world * n_cells / (rhs64 * 1e-3), "unit": "RHS cell-updates/s", "ms": rhs64},
+        # K consecutive steps from the initial state: where the state has
+        # regions of one value (the binary star's atmosphere) later steps cost
+        # more, as disturbances spread through it
+        "evolving": {k: {"steps": K, "ms_per_step": statistics.mean(r["evolve_ms"]), "first_ms": r["evolve_ms"][0],
+                         "last_ms": r["evolve_ms"][-1],
+                         "value": world * n_cells / (statistics.mean(r["evolve_ms"]) * 1e-3)}
+                     for k, r in (("fp64", s64), ("mixed", smx))},
         "mixed": {"value": world * n_cells / (totmx / K * 1e-3), "unit": UNIT, "ms_per_step": totmx / K,
                   "rhs_value": world * n_cells / (rhsmx * 1e-3), "rhs_ms": rhsmx,
                   "speedup_vs_fp64_step": ms_step / (totmx / K), "speedup_vs_fp64_rhs": rhs64 / rhsmx,
@@ -479,7 +506,9 @@ def run_ours(args, rank, world):
         "e2e": {"value": world * n_cells / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes + 8,
                 "how": "oct_hydro_rk_steps_host on pinned host state: H2D copy, RK3 step, D2H copy, per step"},
-        "gpu_launches": launches_per_step(prob, args.recon) * K,
+        # the library's own count of the kernels one step launches (RHS,
+        # dt, combines, and ghost fills unless the combines do them)
+        "gpu_launches": s64["H"].step_launches() * K,
         "clocks": clocks,
         "error_flags": {"fp64": s64["flags"], "mixed": smx["flags"]},
         "launch": {k: {"tile_mode": r["launch"][0], "ctas_per_sm": r["launch"][1], "work_items": r["launch"][2]}
@@ -538,14 +567,6 @@ def mixed_error_table(prob, results, stream):
         m = np.max(np.abs(d_o[idx]))
         out[names[f]] = float(np.max(np.abs(g[idx] - d_o[idx])) / m) if m > 0 else 0.0
     return out
-
-
-def launches_per_step(prob, recon=0):
-    """Kernels of one graph-replayed RK3 step: 3 RHS, the dt reduction, 3
-    combines, 3 ghost fills unless ghosts are given, 3 flux corrections when
-    the batch spans refinement levels, and 3 primitive-variable passes with
-    primitive reconstruction."""
-    return 3 + 1 + 3 + (3 if prob.bc != 0 else 0) + (3 if prob.bc == 3 else 0) + (3 if recon else 0)
 
 
 def _oracle_step_time(workload):
@@ -624,22 +645,39 @@ def run_reference(args):
                                         "d2h_bytes_per_step": 0}}
 
 
-def profile_rhs(args):
-    """args.reps RHS launches of one form on the workload, for a profiler."""
+def profile_run(args):
+    """args.reps launches of one kernel path on the workload, for a profiler:
+    the RHS of one form, a graph-replayed SSP-RK3 step of one form, or the
+    monopole gravity kernel (on the FP64 handle)."""
     import torch
     from paper_2210_06439_gb300 import binding, inputs
     prob = WORKLOADS[args.workload][1](inputs)
     H = binding.Hydro.from_problem(prob, precision=args.precision, recon=args.recon)
     U = torch.from_numpy(prob.U).cuda()
     H.fill_ghosts(U)
-    if args.autotune:
+    if args.autotune and args.profile != "gravity":
         H.autotune(U)
-    d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    if args.profile == "gravity":
+        E3 = int(prob.edge[0]) ** 3
+        out = (torch.empty(prob.n_sub * E3, dtype=torch.float64, device="cuda"),
+               torch.empty(3 * prob.n_sub * E3, dtype=torch.float64, device="cuda"))
+    else:
+        out = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
     for _ in range(args.reps):
-        H.rhs(U, d)
+        with torch.cuda.stream(stream):
+            if args.profile == "step":
+                H.rk_step(U, want_dt=False, stream=stream)
+            elif args.profile == "rhs":
+                H.rhs(U, out, stream=stream)
+            else:
+                H.gravity_monopole(U, *out, G=1.0, r_s=GRAV_RS, stream=stream)
     torch.cuda.synchronize()
-    assert H.error_flags() == 0
-    print("profile-rhs ok", args.workload, "precision", args.precision, "launch", H.launch_info())
+    flags = H.error_flags()
+    # floors may fire inside a step; nothing else may be flagged
+    assert flags & ~binding.OCT_FLAG_FLOOR == 0 and (args.profile == "step" or flags == 0), flags
+    print("profile", args.profile, "ok:", args.workload, "precision", args.precision, "launch", H.launch_info(),
+          "flags", flags)
 
 
 def main():
@@ -652,16 +690,17 @@ def main():
     ap.add_argument("--recon", type=int, default=0, choices=(0, 1),
                     help="reconstructed variables: 0 the conserved fields (the method's default), 1 primitive")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--profile-rhs", action="store_true",
-                    help="only run --reps RHS launches of one form (for profiler captures); no benchmark line")
-    ap.add_argument("--precision", type=int, default=0, choices=(0, 1), help="form for --profile-rhs")
-    ap.add_argument("--reps", type=int, default=3, help="RHS launches for --profile-rhs")
-    ap.add_argument("--no-autotune", dest="autotune", action="store_false", help="--profile-rhs without autotuning")
+    ap.add_argument("--profile", choices=("rhs", "step", "gravity"),
+                    help="only run --reps launches of the RHS, the graph-replayed RK3 step or the monopole "
+                         "gravity kernel (for profiler captures); no benchmark line")
+    ap.add_argument("--precision", type=int, default=0, choices=(0, 1), help="form for --profile rhs|step")
+    ap.add_argument("--reps", type=int, default=3, help="launches for --profile")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false", help="--profile without autotuning")
     args = ap.parse_args()
-    if args.profile_rhs:
+    if args.profile:
         import __graft_entry__
         __graft_entry__.build()
-        profile_rhs(args)
+        profile_run(args)
         return
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

@@ -322,6 +322,15 @@ oct_status oct_hydro_eval_math(int fn, const double *x, double *y, int64_t n, do
  * decreasing work from a counter on the device.  Any pointer may be NULL. */
 oct_status oct_hydro_launch_info(oct_hydro_t h, int *tile_mode, int *ctas_per_sm, int *n_items);
 
+/* Kernel launches of one oct_hydro_rk_step for the current layout and
+ * settings (the three stages of Sec. V-B's "3 hydro solver iterations"):
+ * per stage the RHS kernel (plus the primitive pass with primitive
+ * reconstruction and the flux correction across levels), the combine, and
+ * the ghost fill (none with given ghosts, two passes across levels with
+ * prolongation); plus one dt reduction.  -1 for a NULL handle or one
+ * without a layout. */
+int oct_hydro_step_launches(oct_hydro_t h);
+
 /* Reads and clears the device error flags (OCT_FLAG_*); synchronises.  The
  * paper states no error handling; the flags report what readings R6 and R7
  * of the floors and a non-physical point (rho <= 0, non-finite values) meet

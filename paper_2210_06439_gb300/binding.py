@@ -45,6 +45,7 @@ SIGNATURES = {
     "oct_hydro_autotune": (_I, [_P, _P, _P]),
     "oct_hydro_rhs_dt_noalloc": (_I, [_I, _I, _I, _D, _I, _D, _D, _P, _P, _P, _P, _P]),
     "oct_hydro_launch_info": (_I, [_P, _P, _P, _P]),
+    "oct_hydro_step_launches": (_I, [_P]),
     "oct_hydro_gravity_monopole": (_I, [_P, _P, _D, _D, _P, _P, _P]),
     "oct_hydro_pipe_peaks": (_I, [_D, _P, _P, _P]),
     "oct_hydro_eval_math": (_I, [_I, _P, _P, _I64, _D, _P]),
@@ -242,6 +243,13 @@ class Hydro:
         t, c, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(self.L.oct_hydro_launch_info(self.h, ctypes.addressof(t), ctypes.addressof(c), ctypes.addressof(n)))
         return t.value, c.value, n.value
+
+    def step_launches(self):
+        """Kernel launches of one rk_step for the current layout."""
+        n = self.L.oct_hydro_step_launches(self.h)
+        if n < 0:
+            raise OctError(OCT_E_STATE, "no layout")
+        return n
 
     def tile_mode(self):
         return self.launch_info()[0]

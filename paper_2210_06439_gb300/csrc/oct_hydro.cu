@@ -88,6 +88,7 @@ struct oct_hydro {
     int tile_mode = 0;
     // [form][tile mode], form = precision + 2 * recon
     int ctas_per_sm[4][RHS_MODES] = {};  // the occupancy limit (0: the shape does not fit)
+    int combine_ctas[2] = {1, 1};  // resident combine CTAs per SM: [0] stages 2/3, [1] stage 1
     int cta_use[4][RHS_MODES] = {};      // resident CTAs per SM of the persistent grid (0: the limit)
     int recon = OCT_RECON_CONSERVED;
     double *d_Wprim = nullptr;   // primitive variables of the state (primitive reconstruction)
@@ -191,6 +192,12 @@ static oct_status set_kernel_attrs(oct_hydro *h)
         if (h->ctas_per_sm[form][0] < 1)
             return fail(OCT_E_CUDA, "RHS kernel does not fit on an SM (%zu bytes shared memory)",
                         rhs_smem_bytes(h->nf, form, 0));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->combine_ctas[0], combine_kernel<false>,
+                                                           COMBINE_THREADS, 0));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->combine_ctas[1], combine_kernel<true>,
+                                                           COMBINE_THREADS, 0));
+    h->combine_ctas[0] = std::max(h->combine_ctas[0], 1);
+    h->combine_ctas[1] = std::max(h->combine_ctas[1], 1);
     return OCT_OK;
 }
 
@@ -963,9 +970,13 @@ static oct_status launch_combine(oct_hydro *h, int stage, const double *U0, cons
     A.rho_floor = h->rho_floor;
     A.eps2 = h->eps2;
     A.flags = h->d_flags;
-    // two blocks of 256 threads per subgrid: one cell a thread for edge 8
-    constexpr int parts = 2;
-    combine_kernel<<<(unsigned)(h->n_sub * parts), 256, 0, s>>>(A, parts);
+    // persistent grid over whole subgrids (two cells a thread for edge 8)
+    const int n_items = h->n_sub;
+    const int grid = std::min(n_items, h->n_sm * h->combine_ctas[stage == 1 ? 1 : 0]);
+    if (stage == 1)
+        combine_kernel<true><<<(unsigned)grid, COMBINE_THREADS, 0, s>>>(A, n_items);
+    else
+        combine_kernel<false><<<(unsigned)grid, COMBINE_THREADS, 0, s>>>(A, n_items);
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;
 }
@@ -988,6 +999,20 @@ static oct_status enqueue_step(oct_hydro *h, double *U, cudaStream_t s)
     if ((st = launch_combine(h, 3, U, W, U, s)) != OCT_OK) return st;
     if ((st = launch_ghosts(h, U, s)) != OCT_OK) return st;
     return OCT_OK;
+}
+
+extern "C" int oct_hydro_step_launches(oct_hydro_t h)
+{
+    if (!h || !h->layout_ok)
+        return -1;
+    int per_rhs = 1 + (h->recon == OCT_RECON_PRIMITIVE ? 1 : 0) +
+                  (h->bc == OCT_BC_AMR && h->n_corr_cells > 0 ? 1 : 0);
+    int per_fill = 0;
+    if (h->bc == OCT_BC_AMR)
+        per_fill = h->has_prolong ? 2 : 1;
+    else if (h->bc != OCT_BC_GIVEN)
+        per_fill = 1;
+    return 3 * per_rhs + 1 + 3 + 3 * per_fill;
 }
 
 extern "C" oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_used_host_out, void *cuda_stream)

@@ -71,81 +71,152 @@ struct CombineArgs {
 //   stage 3: out = 1/3 U0 + 2/3 (X + dt L)
 // then the floors rho >= rho_floor, rho_i >= 0, the tau re-synchronisation
 // tau = e_int^(1/gamma) where e_int = E - |s|^2/(2 rho) > eps2 E, and tau >= 0.
-// `parts` blocks per subgrid (block b works on subgrid b / parts), each
-// thread on interior cells c = part * blockDim + threadIdx, c + parts *
-// blockDim, ... (x fastest, so a warp reads whole interior rows); all loads
-// of a cell are issued before its stores.
-// Three CTAs per SM (80 registers): the kernel waits on memory, and 24 warps
-// per SM hide more of it than the 16 that 103 registers allowed.
-__global__ void __launch_bounds__(256, 3) combine_kernel(CombineArgs A, int parts)
+// The arithmetic of one cell (xv, lv, u0: its X, L and U0 values; u0 unused
+// in stage 1); returns true when a floor fired.
+template <bool S1>
+__device__ __forceinline__ bool combine_cell(const CombineArgs &A, int nf, double a, double b, double dt,
+                                             const double (&xv)[MAXNF], const double (&lv)[MAXNF],
+                                             const double (&u0)[MAXNF], double (&u)[MAXNF])
 {
-    const int s = blockIdx.x / parts, part = blockIdx.x - s * parts;
-    const int E = A.edge[s], B = E + 2 * NG;
-    const long long FS = (long long)B * B * B;
-    const int E3 = E * E * E;
-    const long long gbase = A.off[s], lbase = A.doff[s];
+#pragma unroll
+    for (int f = 0; f < MAXNF; f++)
+        if (f < nf) {
+            const double x1 = xv[f] + dt * lv[f];
+            u[f] = S1 ? x1 : a * u0[f] + b * x1;
+        }
+    bool fired = false;
+    if (u[F_RHO] < A.rho_floor) {
+        u[F_RHO] = A.rho_floor;
+        fired = true;
+    }
+#pragma unroll
+    for (int f = F_SPC; f < MAXNF; f++)
+        if (f < nf) {
+            const int hi = __double2hiint(u[f]);
+            if (hi < 0 && ((hi & 0x7FFFFFFF) | __double2loint(u[f])) != 0) {  // negative, not -0
+                u[f] = 0.0;
+                fired = true;
+            }
+        }
+    const double ei =
+        u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) * rcp_nr(u[F_RHO]);
+    if (ei > A.eps2 * u[F_EGAS])
+        u[F_TAU] = tau_of_eint(ei, A.gamma);
+    if (u[F_TAU] < 0.0) {
+        u[F_TAU] = 0.0;
+        fired = true;
+    }
+    return fired;
+}
+
+__device__ __forceinline__ int nb_slot(int dx, int dy, int dz)
+{
+    int n = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+    return n > 13 ? n - 1 : n;
+}
+
+// The cells of one thread of the persistent combine grid: items
+// blockIdx.x, blockIdx.x + gridDim.x, ... of n_items = n_sub * parts (item i:
+// subgrid i / parts, part i % parts), and within an item the interior cells
+// c = part * blockDim + threadIdx + k * parts * blockDim (x fastest, so a warp
+// reads whole interior rows).
+struct CombineCursor {
+    int item, c, E, E3, B;
+    unsigned mE;
+    long long gbase, lbase, FS;
+    __device__ bool next(const CombineArgs &A, int parts, int n_items)
+    {
+        if (c >= 0) {
+            c += parts * (int)blockDim.x;
+            if (c < E3)
+                return true;
+            item += gridDim.x;
+        }
+        for (; item < n_items; item += gridDim.x) {
+            const int s = item / parts, part = item - s * parts;
+            E = A.edge[s];
+            E3 = E * E * E;
+            B = E + 2 * NG;
+            FS = (long long)B * B * B;
+            mE = rcp_div(E);
+            gbase = A.off[s];
+            lbase = A.doff[s];
+            c = part * (int)blockDim.x + (int)threadIdx.x;
+            if (c < E3)
+                return true;
+        }
+        return false;
+    }
+    __device__ long long gi() const
+    {
+        const int zy = div_by(c, mE), z = div_by(zy, mE);
+        return gbase + ((long long)(z + NG) * B + (zy - z * E + NG)) * B + (c - zy * E + NG);
+    }
+};
+
+constexpr int COMBINE_THREADS = 256;
+
+// The combine over all interior cells, software-pipelined: a thread issues
+// the loads of its next cell before the arithmetic of the current one, so
+// that each CTA keeps its memory traffic and its FP64 work in flight at the
+// same time (with one cell per thread and CTA, the CTAs of an SM load, then
+// compute, then store in step with each other, and the launch takes the sum
+// of its memory time and its FP64 time).  Persistent grid of as many CTAs as
+// fit on the GPU, whole subgrids as items.
+template <bool S1>
+__global__ void __launch_bounds__(COMBINE_THREADS, 1) combine_kernel(CombineArgs A, int n_items)
+{
     const double dt = A.dt[0];
-    double a, b;
-    if (A.stage == 1) {
-        a = 0.0;
-        b = 1.0;
-    } else if (A.stage == 2) {
-        a = 0.75;
-        b = 0.25;
-    } else {
-        a = 1.0 / 3.0;
-        b = 2.0 / 3.0;
-    }
-    const unsigned m_E = rcp_div(E);
-    for (int c = part * blockDim.x + threadIdx.x; c < E3; c += parts * blockDim.x) {
-        const int zy = div_by(c, m_E), z = div_by(zy, m_E);
-        const int x = c - zy * E, y = zy - z * E;
-        const long long gi = gbase + ((long long)(z + NG) * B + (y + NG)) * B + (x + NG);
-        const long long li = lbase + c;
-        double xv[MAXNF], lv[MAXNF], u0[MAXNF];
+    const double a = A.stage == 2 ? 0.75 : 1.0 / 3.0;
+    const double b = A.stage == 2 ? 0.25 : 2.0 / 3.0;
+    const int nf = A.nf;
+    CombineCursor cur;
+    cur.item = blockIdx.x;
+    cur.c = -1;
+    bool have = cur.next(A, 1, n_items);
+    double xp[MAXNF], lp[MAXNF], vp[MAXNF], xq[MAXNF], lq[MAXNF], vq[MAXNF];
+    long long gp = 0, fsp = 0, gq = 0, fsq = 0;
+    auto load = [&](double (&xv)[MAXNF], double (&lv)[MAXNF], double (&u0)[MAXNF], long long &g, long long &fs) {
+        g = cur.gi();
+        fs = cur.FS;
+        const long long li = cur.lbase + cur.c;
 #pragma unroll
         for (int f = 0; f < MAXNF; f++)
-            if (f < A.nf) {
-                xv[f] = A.X[gi + f * FS];
-                lv[f] = A.L[li + f * E3];
-                u0[f] = A.stage == 1 ? 0.0 : A.U0[gi + f * FS];
+            if (f < nf) {
+                xv[f] = A.X[g + f * fs];
+                lv[f] = A.L[li + f * cur.E3];
+                if (!S1)
+                    u0[f] = A.U0[g + f * fs];
             }
+    };
+    if (have)
+        load(xp, lp, vp, gp, fsp);
+    bool fired = false;
+    while (have) {
+        // the next cell's loads, then this cell's arithmetic and stores
+        const bool more = cur.next(A, 1, n_items);
+        if (more)
+            load(xq, lq, vq, gq, fsq);
         double u[MAXNF];
+        fired |= combine_cell<S1>(A, nf, a, b, dt, xp, lp, vp, u);
 #pragma unroll
         for (int f = 0; f < MAXNF; f++)
-            if (f < A.nf) {
-                const double x1 = xv[f] + dt * lv[f];
-                u[f] = (A.stage == 1) ? x1 : a * u0[f] + b * x1;
-            }
-        bool fired = false;
-        if (u[F_RHO] < A.rho_floor) {
-            u[F_RHO] = A.rho_floor;
-            fired = true;
-        }
+            if (f < nf)
+                A.out[gp + f * fsp] = u[f];
+        if (more) {
 #pragma unroll
-        for (int f = F_SPC; f < MAXNF; f++)
-            if (f < A.nf) {
-                const int hi = __double2hiint(u[f]);
-                if (hi < 0 && ((hi & 0x7FFFFFFF) | __double2loint(u[f])) != 0) {  // negative, not -0
-                    u[f] = 0.0;
-                    fired = true;
-                }
+            for (int f = 0; f < MAXNF; f++) {
+                xp[f] = xq[f];
+                lp[f] = lq[f];
+                vp[f] = vq[f];
             }
-        const double ei =
-            u[F_EGAS] - 0.5 * (u[F_SX] * u[F_SX] + u[F_SY] * u[F_SY] + u[F_SZ] * u[F_SZ]) * rcp_nr(u[F_RHO]);
-        if (ei > A.eps2 * u[F_EGAS])
-            u[F_TAU] = tau_of_eint(ei, A.gamma);
-        if (u[F_TAU] < 0.0) {
-            u[F_TAU] = 0.0;
-            fired = true;
+            gp = gq;
+            fsp = fsq;
         }
-#pragma unroll
-        for (int f = 0; f < MAXNF; f++)
-            if (f < A.nf)
-                A.out[gi + f * FS] = u[f];
-        if (fired)
-            atomicOr(A.flags, 2u);
+        have = more;
     }
+    if (fired)
+        atomicOr(A.flags, 2u);
 }
 
 // The ghost shell of a subgrid of edge E, enumerated as: the two z slabs
@@ -185,12 +256,6 @@ struct GhostShell {
         }
     }
 };
-
-__device__ __forceinline__ int nb_slot(int dx, int dy, int dz)
-{
-    int n = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-    return n > 13 ? n - 1 : n;
-}
 
 // Ghost fill on a uniform level, one block per subgrid: each ghost cell
 // copies the matching interior cell of the neighbour subgrid; along an axis

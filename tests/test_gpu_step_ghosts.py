@@ -1,0 +1,111 @@
+"""Ghost cells after an RK3 step on a uniform level, over the arrangements a
+neighbour table can describe: the stepped state must match the oracle's
+step, and its ghost cells must be exactly the oracle's ghost fill of its
+interior (the copy of the matching neighbour cell, or of the nearest own cell
+along axes without a face neighbour), bitwise.  Arrangements: one subgrid
+wrapping onto itself; two and three subgrids along an axis (a two-wide
+periodic axis links both faces to the same subgrid); non-cubic boxes;
+periodic along some axes and open along the others; outflow on every side;
+edges 8, 12 and 16; a table with a one-way link; and three graph-replayed
+steps in a row.  Also the library's count of the kernels one step launches."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_06439_gb300 import inputs
+from tests.helpers import e3s, field_errors, interior_layout, oracle_filled
+
+pytestmark = pytest.mark.gpu
+
+
+def _box(nx, ny, nz, E=8, periodic=True, seed=7):
+    n_cells = nx * ny * nz * E ** 3
+    f = inputs._noisy_gas_law(seed, np.arange(n_cells, dtype=np.uint64))
+    f = f.reshape(11, nz * E, ny * E, nx * E)
+    bc = 1 if periodic is True else 2
+    return inputs._tile_global("step_ghosts", f, (nx, ny, nz), E, 1.0 / (max(nx, ny, nz) * E), bc, periodic)
+
+
+def _step_and_check(p, precision=0):
+    import torch
+    from paper_2210_06439_gb300 import binding
+    ref = oracle_filled(p)
+    U0 = ref.U.copy()
+    dt_o, fired, st = oracle.rk3_step(ref.edge, ref.off, ref.dx, ref.nf, ref.U, bc=p.bc, nbr=p.nbr)
+    assert st == 0
+    H = binding.Hydro.from_problem(p, precision=precision)
+    assert H.step_launches() == 10  # 3 RHS, the dt reduction, 3 combines, 3 ghost fills
+    U = torch.from_numpy(U0).cuda()
+    dt_g = H.rk_step(U)
+    flags = H.error_flags()
+    assert flags & ~binding.OCT_FLAG_FLOOR == 0, flags
+    assert dt_g == pytest.approx(dt_o, rel=1e-12 if precision == 0 else 2e-6)
+    got = U.cpu().numpy()
+    errs = field_errors(interior_layout(got, p), interior_layout(ref.U, p), p.nf, e3s(p))
+    assert np.all(errs <= (1e-12 if precision == 0 else 1e-6)), errs
+    chk = p.copy()
+    chk.U[:] = got
+    oracle.ghost_fill(int(p.edge[0]), chk.off, chk.nf, chk.nbr, chk.U)
+    assert np.array_equal(chk.U, got), np.flatnonzero(chk.U != got)[:10]
+    return got
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 1, 1), (3, 2, 1), (2, 2, 2), (1, 3, 2)])
+def test_periodic_arrangements(shape):
+    _step_and_check(_box(*shape, periodic=True))
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 1, 1), (2, 3, 2), (3, 3, 3)])
+def test_outflow_arrangements(shape):
+    _step_and_check(_box(*shape, periodic=False))
+
+
+@pytest.mark.parametrize("periodic", [(True, False, False), (False, True, True), (True, True, False)])
+def test_periodic_along_some_axes(periodic):
+    _step_and_check(_box(3, 2, 2, periodic=periodic))
+
+
+@pytest.mark.parametrize("E", [12, 16])
+@pytest.mark.parametrize("periodic", [True, False])
+def test_larger_edges(E, periodic):
+    _step_and_check(_box(2, 2, 1, E=E, periodic=periodic))
+
+
+def test_mixed_form():
+    _step_and_check(_box(3, 2, 2, periodic=(True, False, True)), precision=1)
+
+
+def test_one_way_link():
+    """Subgrid 1 of a 2x1x1 outflow row does not list subgrid 0 as its -x
+    neighbour (so it clamps those ghosts to its own cells) while subgrid 0
+    lists subgrid 1 as its +x neighbour."""
+    p = _box(2, 1, 1, periodic=False)
+    nbr = p.nbr.reshape(2, 26).copy()
+    slot = inputs.nb_slot(-1, 0, 0)
+    assert nbr[1, slot] == 0
+    nbr[1, slot] = -1
+    p.nbr = nbr.ravel()
+    _step_and_check(p)
+
+
+def test_steps_replay_and_match_the_oracle_over_several_steps():
+    """Three graph-replayed steps on an outflow box against three oracle
+    steps."""
+    import torch
+    from paper_2210_06439_gb300 import binding
+    p = _box(3, 2, 2, periodic=False, seed=11)
+    ref = oracle_filled(p)
+    U = torch.from_numpy(ref.U.copy()).cuda()
+    H = binding.Hydro.from_problem(p)
+    for _ in range(3):
+        dt_o, _, st = oracle.rk3_step(ref.edge, ref.off, ref.dx, ref.nf, ref.U, bc=p.bc, nbr=p.nbr)
+        assert st == 0
+        dt_g = H.rk_step(U)
+        assert dt_g == pytest.approx(dt_o, rel=1e-12)
+    got = U.cpu().numpy()
+    errs = field_errors(interior_layout(got, p), interior_layout(ref.U, p), p.nf, e3s(p))
+    assert np.all(errs <= 1e-12), errs
+    chk = p.copy()
+    chk.U[:] = got
+    oracle.ghost_fill(8, chk.off, chk.nf, chk.nbr, chk.U)
+    assert np.array_equal(chk.U, got)
