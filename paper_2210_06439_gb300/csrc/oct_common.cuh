@@ -66,6 +66,9 @@ struct RhsArgs {
     // between launches; null: static round robin)
     const int *order;
     int *ticket;
+    // per subgrid: 1 when its ghosted block holds one value per field and
+    // uniform_subgrid_kernel has written its RHS and a_max (null: no such test)
+    const int *sub_uniform;
 };
 
 // q / d for the small divisors of the kernels' index arithmetic (tile widths,

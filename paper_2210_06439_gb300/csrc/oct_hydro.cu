@@ -94,6 +94,7 @@ struct oct_hydro {
     double *d_Wprim = nullptr;   // primitive variables of the state (primitive reconstruction)
     // device memory
     int *d_edge = nullptr, *d_nbr = nullptr, *d_item_begin = nullptr;
+    int *d_sub_uniform = nullptr;  // per subgrid: ghosted block of one value per field (set before each RHS)
     long long *d_off = nullptr, *d_doff = nullptr;
     double *d_dx = nullptr;
     WorkItem *d_items = nullptr;
@@ -159,6 +160,7 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_edge);
     dfree(h->d_nbr);
     dfree(h->d_item_begin);
+    dfree(h->d_sub_uniform);
     dfree(h->d_off);
     dfree(h->d_doff);
     dfree(h->d_dx);
@@ -279,6 +281,8 @@ static oct_status upload_items(oct_hydro *h)
     dfree(h->d_item_begin);
     dfree(h->d_amax_tile);
     dfree(h->d_order);
+    dfree(h->d_sub_uniform);
+    CUDA_TRY(cudaMalloc(&h->d_sub_uniform, sizeof(int) * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_items, sizeof(WorkItem) * h->items.size()));
     CUDA_TRY(cudaMemcpy(h->d_items, h->items.data(), sizeof(WorkItem) * h->items.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&h->d_item_begin, sizeof(int) * h->item_begin.size()));
@@ -840,9 +844,16 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
     A.face_slot = reflux ? h->d_face_slot : nullptr;
     A.order = h->d_order;
     A.ticket = h->d_ticket;
+    A.sub_uniform = nullptr;
     const int form = form_of(h), mode = h->tile_mode;
     if (h->items_mode != mode || h->items_grid != grid_ctas(h))
         return fail(OCT_E_STATE, "work items were cut for another launch shape");
+    if (h->recon != OCT_RECON_PRIMITIVE && !reflux) {
+        // subgrids whose ghosted block is one value per field: RHS and a_max
+        // written here, skipped by the RHS kernel
+        CUDA_TRY(uniform_launch(h->precision, h->n_sub, st, A, h->d_item_begin, h->d_sub_uniform));
+        A.sub_uniform = h->d_sub_uniform;
+    }
     int grid = std::min<int>(A.n_items, grid_ctas(h));
     CUDA_TRY(rhs_launch(form, mode, grid, st, A));
     CUDA_TRY(cudaGetLastError());
@@ -1005,8 +1016,11 @@ extern "C" int oct_hydro_step_launches(oct_hydro_t h)
 {
     if (!h || !h->layout_ok)
         return -1;
-    int per_rhs = 1 + (h->recon == OCT_RECON_PRIMITIVE ? 1 : 0) +
-                  (h->bc == OCT_BC_AMR && h->n_corr_cells > 0 ? 1 : 0);
+    const bool reflux = h->bc == OCT_BC_AMR && h->n_corr_cells > 0;
+    // the RHS kernel, with the primitive pass before it (primitive
+    // reconstruction) or else the whole-subgrid uniform test, and the flux
+    // correction after it across levels
+    int per_rhs = 1 + (h->recon == OCT_RECON_PRIMITIVE ? 1 : (reflux ? 0 : 1)) + (reflux ? 1 : 0);
     int per_fill = 0;
     if (h->bc == OCT_BC_AMR)
         per_fill = h->has_prolong ? 2 : 1;
@@ -1531,6 +1545,7 @@ extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_s
     A.face_slot = nullptr;
     A.order = nullptr;
     A.ticket = nullptr;
+    A.sub_uniform = nullptr;  // the kernel's own per-item uniform test
     int grid = std::min(n_items, D->n_sm * D->ctas[precision]);
     CUDA_TRY(rhs_launch(precision, 0, grid, s, A));
     dt_kernel<<<1, 1024, 0, s>>>(n_items, d_items, dx, d_amax, cfl, nullptr, dt);

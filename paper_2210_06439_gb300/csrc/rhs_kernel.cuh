@@ -518,7 +518,8 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
     // work items: the first by block index, the rest from the ticket counter
     // in execution order (largest first), so that CTAs which finish early take
     // the remaining items; without a ticket, a static round robin
-    __shared__ int s_next;
+    __shared__ int s_next[2];  // by parity: an item that is skipped has no barrier of its own
+    int par = 0;
     // whether phase A of a line group met a stencil of one value (uniform
     // data), by group parity: set in phase A, read after its barrier, cleared
     // for the group after next during phase B2.  Only then do phases B1 and
@@ -531,6 +532,16 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
         const int it = A.order != nullptr ? A.order[k] : k;
         const WorkItem W = A.items[it];
         const int s = W.s, x0 = W.x0, y0 = W.y0, tx = W.txty & 0xFF, ty = (W.txty >> 8) & 0xFF;
+        if (A.sub_uniform != nullptr && A.sub_uniform[s] != 0) {
+            // the subgrid's whole ghosted block holds one value per field: its
+            // RHS and a_max were written by uniform_subgrid_kernel
+            if (tid == 0)
+                s_next[par] = A.ticket != nullptr ? (int)gridDim.x + atomicAdd(A.ticket, 1) : k + (int)gridDim.x;
+            __syncthreads();
+            k = s_next[par];
+            par ^= 1;
+            continue;
+        }
         const int E = A.edge[s], B = E + 2 * NG;
         const long long FS = (long long)B * B * B;
         const double *Ub = A.U + A.off[s];
@@ -1105,10 +1116,11 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
             for (int w = 0; w < NT / 32; w++)
                 m = fmax(m, red[w]);
             A.amax_tile[it] = m;
-            s_next = A.ticket != nullptr ? (int)gridDim.x + atomicAdd(A.ticket, 1) : k + (int)gridDim.x;
+            s_next[par] = A.ticket != nullptr ? (int)gridDim.x + atomicAdd(A.ticket, 1) : k + (int)gridDim.x;
         }
         __syncthreads();
-        k = s_next;
+        k = s_next[par];
+        par ^= 1;
     }
     if (A.ticket != nullptr && tid == 0) {
         // every CTA has drawn its last ticket before it counts itself done: the
@@ -1121,6 +1133,69 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
     }
     if (bad)
         atomicOr(A.flags, 1u);
+}
+
+// Whole-subgrid uniform test ahead of the RHS kernel (conserved
+// reconstruction, no boundary face fluxes wanted): when the ghosted block of
+// subgrid s holds one value per field (bitwise), every work item of s would
+// take the uniform-column path of rhs_kernel, so this kernel writes what that
+// path writes -- RHS -0.0 for every cell, and a_max = max_k |v_k| + c of the
+// state, from the same primitive function in the form's precision, for each
+// of the subgrid's items -- and sets sub_uniform[s], which makes rhs_kernel
+// skip those items.  One CTA per subgrid streams the block field by field
+// (each field one contiguous run of B^3 doubles, read as double2), many CTAs
+// per SM, leaving at the first field that differs.
+constexpr int UNI_THREADS = 256;
+template <class T>
+__global__ void __launch_bounds__(UNI_THREADS) uniform_subgrid_kernel(RhsArgs A, const int *item_begin,
+                                                                      int *sub_uniform)
+{
+    const int s = blockIdx.x, tid = threadIdx.x;
+    const int E = A.edge[s], B = E + 2 * NG;
+    const int n2 = B * B * B / 2;  // B is even: whole double2 per field
+    const double *Ub = A.U + A.off[s];
+    const int nf = A.nf;
+    int diff = 0;
+    for (int f = 0; f < nf && !diff; f++) {
+        const double *fb = Ub + (long long)f * 2 * n2;
+        const double2 *f2 = reinterpret_cast<const double2 *>(fb);
+        const double ref = __ldg(fb);
+#pragma unroll 4
+        for (int v = tid; v < n2; v += UNI_THREADS) {
+            const double2 w = __ldg(f2 + v);
+            diff |= (bit_diff(w.x, ref) | bit_diff(w.y, ref)) != 0u;
+        }
+        diff = __syncthreads_or(diff);
+    }
+    if (diff) {
+        if (tid == 0)
+            sub_uniform[s] = 0;
+        return;
+    }
+    const T gamma = Num<T>::from_d(A.gamma);
+    const T gm1 = Num<T>::from_d(A.gamma - 1.0);
+    const T ggm1 = Num<T>::from_d(A.gamma * (A.gamma - 1.0));
+    const T eps1 = Num<T>::from_d(A.eps1);
+    T qh[6], v[3], p, c;
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+        qh[f] = Num<T>::from_d(__ldg(Ub + (long long)f * 2 * n2));
+    bool bad = false;
+    prim_point(qh, gamma, gm1, ggm1, eps1, v, p, c, bad);
+    const T a = max_nonneg(max_nonneg(fabs(v[0]) + c, fabs(v[1]) + c), fabs(v[2]) + c);
+    const double amax = Num<T>::to_d(a);
+    // the subgrid's RHS: nf E^3 doubles from doff[s] (an even count and offset)
+    double2 *d2 = reinterpret_cast<double2 *>(A.dUdt + A.doff[s]);
+    const int m2 = nf * E * E * E / 2;
+    for (int q = tid; q < m2; q += UNI_THREADS)
+        d2[q] = make_double2(-0.0, -0.0);
+    for (int t = item_begin[s] + tid; t < item_begin[s + 1]; t += UNI_THREADS)
+        A.amax_tile[t] = amax;
+    if (tid == 0) {
+        sub_uniform[s] = 1;
+        if (bad)
+            atomicOr(A.flags, 1u);
+    }
 }
 
 }  // namespace octh

@@ -169,6 +169,48 @@ def test_binary_star_small(precision):
     _check_rhs(inputs.binary_star(nsub=4), precision)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uniform_subgrids_take_the_whole_block_test(precision):
+    """The 32^3 binary star (64 subgrids, 48 of them atmosphere): the
+    subgrids whose ghosted block holds one value per field (found here with
+    numpy) get RHS -0.0, sign bit set, in every cell, as the oracle's full
+    formula gives, and the oracle's a_max; the handle's RHS (whole-subgrid
+    test ahead of the kernel) and the allocation-free call (the kernel's
+    per-item test) agree on them bitwise and elsewhere within the form's
+    tolerance."""
+    torch = _torch()
+    from paper_2210_06439_gb300 import binding
+    p = oracle_filled(inputs.binary_star(nsub=4))
+    nf, E = p.nf, 8
+    blocks = [p.block(s) for s in range(p.n_sub)]
+    uni = np.array([all(np.all(b[f].view(np.int64) == b[f].ravel()[0].view(np.int64)) for f in range(nf))
+                    for b in blocks])
+    assert 8 <= uni.sum() < p.n_sub
+    d_o, am_o, _ = oracle.rhs(p.edge, p.off, p.dx, p.nf, p.U)
+    H = _hydro(p, precision)
+    U = torch.from_numpy(p.U).cuda()
+    d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+    am = torch.zeros(p.n_sub, dtype=torch.float64, device="cuda")
+    H.rhs(U, d, am)
+    L = binding.load()
+    dx = torch.from_numpy(np.ascontiguousarray(p.dx)).cuda()
+    d2 = torch.full((H.rhs_len,), float("nan"), dtype=torch.float64, device="cuda")
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = L.oct_hydro_rhs_dt_noalloc(p.n_sub, E, p.n_species, p.gamma, precision, 0.4, 1e-3, U.data_ptr(),
+                                    dx.data_ptr(), d2.data_ptr(), dt.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
+    assert st == binding.OCT_OK
+    torch.cuda.synchronize()
+    g, g2 = d.cpu().numpy().reshape(p.n_sub, -1), d2.cpu().numpy().reshape(p.n_sub, -1)
+    o = d_o.reshape(p.n_sub, -1)
+    neg0 = np.array([-0.0]).view(np.int64)[0]
+    assert np.all(o[uni].view(np.int64) == neg0)
+    assert np.all(g[uni].view(np.int64) == neg0) and np.all(g2[uni].view(np.int64) == neg0)
+    np.testing.assert_allclose(am.cpu().numpy()[uni], am_o[uni], rtol=1e-12 if precision == 0 else MIXED_SPEED_RTOL)
+    errs = field_errors(g2.ravel(), g.ravel(), p.nf, e3s(p))
+    assert np.all(errs <= TOL[precision]), errs
+
+
 def test_nonphysical_input_sets_flag_without_trap():
     torch = _torch()
     p = oracle_filled(inputs.periodic_box(nsub=2))
