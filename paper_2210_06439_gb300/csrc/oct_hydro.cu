@@ -94,7 +94,12 @@ struct oct_hydro {
     double *d_Wprim = nullptr;   // primitive variables of the state (primitive reconstruction)
     // device memory
     int *d_edge = nullptr, *d_nbr = nullptr, *d_item_begin = nullptr;
-    int *d_sub_uniform = nullptr;  // per subgrid: ghosted block of one value per field (set before each RHS)
+    // per subgrid, set by the whole-subgrid uniform test before each RHS: the
+    // ghosted block held one value per field ([0..n) the step's state, as of
+    // the first stage; [n..2n) the stage state of stages 2 and 3)
+    int *d_sub_uniform = nullptr;
+    int *d_changed = nullptr;  // per subgrid: interior changed by the last combine (stages 2 and 3)
+    bool uni_test = false;     // the last RHS launch ran the uniform test
     long long *d_off = nullptr, *d_doff = nullptr;
     double *d_dx = nullptr;
     WorkItem *d_items = nullptr;
@@ -161,6 +166,7 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_nbr);
     dfree(h->d_item_begin);
     dfree(h->d_sub_uniform);
+    dfree(h->d_changed);
     dfree(h->d_off);
     dfree(h->d_doff);
     dfree(h->d_dx);
@@ -282,7 +288,9 @@ static oct_status upload_items(oct_hydro *h)
     dfree(h->d_amax_tile);
     dfree(h->d_order);
     dfree(h->d_sub_uniform);
-    CUDA_TRY(cudaMalloc(&h->d_sub_uniform, sizeof(int) * std::max(1, h->n_sub)));
+    dfree(h->d_changed);
+    CUDA_TRY(cudaMalloc(&h->d_sub_uniform, sizeof(int) * 2 * std::max(1, h->n_sub)));
+    CUDA_TRY(cudaMalloc(&h->d_changed, sizeof(int) * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_items, sizeof(WorkItem) * h->items.size()));
     CUDA_TRY(cudaMemcpy(h->d_items, h->items.data(), sizeof(WorkItem) * h->items.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&h->d_item_begin, sizeof(int) * h->item_begin.size()));
@@ -814,7 +822,9 @@ static oct_status check_ptr(const void *p, const char *name)
 }
 
 // Launches the RHS kernel of the handle's precision.
-static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaStream_t st)
+// uni_slot: which half of the per-subgrid uniform flags the whole-subgrid
+// test writes (1 for the stage states of stages 2 and 3 of a step).
+static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaStream_t st, int uni_slot = 0)
 {
     RhsArgs A;
     A.U = U;
@@ -848,11 +858,13 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
     const int form = form_of(h), mode = h->tile_mode;
     if (h->items_mode != mode || h->items_grid != grid_ctas(h))
         return fail(OCT_E_STATE, "work items were cut for another launch shape");
-    if (h->recon != OCT_RECON_PRIMITIVE && !reflux) {
+    h->uni_test = h->recon != OCT_RECON_PRIMITIVE && !reflux;
+    if (h->uni_test) {
         // subgrids whose ghosted block is one value per field: RHS and a_max
         // written here, skipped by the RHS kernel
-        CUDA_TRY(uniform_launch(h->precision, h->n_sub, st, A, h->d_item_begin, h->d_sub_uniform));
-        A.sub_uniform = h->d_sub_uniform;
+        int *flags = h->d_sub_uniform + (size_t)uni_slot * h->n_sub;
+        CUDA_TRY(uniform_launch(h->precision, h->n_sub, st, A, h->d_item_begin, flags));
+        A.sub_uniform = flags;
     }
     int grid = std::min<int>(A.n_items, grid_ctas(h));
     CUDA_TRY(rhs_launch(form, mode, grid, st, A));
@@ -933,7 +945,8 @@ extern "C" oct_status oct_hydro_max_dt(oct_hydro_t h, const double *U, double *d
     return OCT_OK;
 }
 
-static oct_status launch_ghosts(oct_hydro *h, double *U, cudaStream_t s)
+// changed: per-subgrid flags of the combine just before (null: fill all).
+static oct_status launch_ghosts(oct_hydro *h, double *U, cudaStream_t s, const int *changed = nullptr)
 {
     if (h->bc == OCT_BC_GIVEN)
         return OCT_OK;
@@ -946,7 +959,7 @@ static oct_status launch_ghosts(oct_hydro *h, double *U, cudaStream_t s)
         }
         return OCT_OK;
     }
-    ghost_fill_kernel<<<h->n_sub, 256, 0, s>>>(U, h->edge[0], h->d_off, h->nf, h->d_nbr, h->d_flags);
+    ghost_fill_kernel<<<h->n_sub, 256, 0, s>>>(U, h->edge[0], h->d_off, h->nf, h->d_nbr, h->d_flags, changed);
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;
 }
@@ -981,6 +994,13 @@ static oct_status launch_combine(oct_hydro *h, int stage, const double *U0, cons
     A.rho_floor = h->rho_floor;
     A.eps2 = h->eps2;
     A.flags = h->d_flags;
+    // the uniform flags of this stage's RHS inputs (stage 1: U; stages 2 and
+    // 3: the stage state, and U as of stage 1), when the RHS ran that test
+    A.uni_u0 = h->uni_test ? h->d_sub_uniform : nullptr;
+    A.uni_x = h->uni_test ? h->d_sub_uniform + (stage == 1 ? 0 : h->n_sub) : nullptr;
+    A.changed = stage == 1 ? nullptr : h->d_changed;
+    A.out_is_x = out == X;
+    A.out_is_u0 = out == U0;
     // persistent grid over whole subgrids (two cells a thread for edge 8)
     const int n_items = h->n_sub;
     const int grid = std::min(n_items, h->n_sm * h->combine_ctas[stage == 1 ? 1 : 0]);
@@ -1001,14 +1021,17 @@ static oct_status enqueue_step(oct_hydro *h, double *U, cudaStream_t s)
         CUDA_TRY(cudaMemcpyAsync(W, U, sizeof(double) * h->state_len, cudaMemcpyDeviceToDevice, s));
     if ((st = launch_rhs(h, U, h->d_L, s)) != OCT_OK) return st;
     if ((st = launch_dt(h, s)) != OCT_OK) return st;
+    // the ghost fills after stages 2 and 3 leave alone the subgrids whose
+    // neighbourhood the combine did not change (W's ghosts are valid after
+    // stage 1's fill, U's on entry)
     if ((st = launch_combine(h, 1, U, U, W, s)) != OCT_OK) return st;
     if ((st = launch_ghosts(h, W, s)) != OCT_OK) return st;
-    if ((st = launch_rhs(h, W, h->d_L, s)) != OCT_OK) return st;
+    if ((st = launch_rhs(h, W, h->d_L, s, 1)) != OCT_OK) return st;
     if ((st = launch_combine(h, 2, U, W, W, s)) != OCT_OK) return st;
-    if ((st = launch_ghosts(h, W, s)) != OCT_OK) return st;
-    if ((st = launch_rhs(h, W, h->d_L, s)) != OCT_OK) return st;
+    if ((st = launch_ghosts(h, W, s, h->d_changed)) != OCT_OK) return st;
+    if ((st = launch_rhs(h, W, h->d_L, s, 1)) != OCT_OK) return st;
     if ((st = launch_combine(h, 3, U, W, U, s)) != OCT_OK) return st;
-    if ((st = launch_ghosts(h, U, s)) != OCT_OK) return st;
+    if ((st = launch_ghosts(h, U, s, h->d_changed)) != OCT_OK) return st;
     return OCT_OK;
 }
 

@@ -63,6 +63,14 @@ struct CombineArgs {
     int nf;
     double gamma, rho_floor, eps2;
     unsigned *flags;
+    // Optional (null: every subgrid cell by cell): per subgrid, 1 when the
+    // ghosted block of X (uni_x) and of U0 (uni_u0) held one value per field
+    // at this stage's RHS (its L is then -0.0 everywhere), and the per-subgrid
+    // "interior of out changed" flags this combine writes (stages 2 and 3,
+    // whose out aliases X or U0; null otherwise).
+    const int *uni_x, *uni_u0;
+    int *changed;
+    int out_is_x, out_is_u0;
 };
 
 // One SSP-RK3 combine (Shu-Osher) on the interior:
@@ -120,6 +128,14 @@ __device__ __forceinline__ int nb_slot(int dx, int dy, int dz)
 // subgrid i / parts, part i % parts), and within an item the interior cells
 // c = part * blockDim + threadIdx + k * parts * blockDim (x fastest, so a warp
 // reads whole interior rows).
+// Whether subgrid s takes the combine's uniform pass: its X and (for stages
+// 2 and 3) U0 blocks were found to hold one value per field, so every cell
+// of it has the same inputs (L = -0.0 included) and the same result.
+__device__ __forceinline__ bool uniform_item(const CombineArgs &A, int s)
+{
+    return A.uni_x != nullptr && A.uni_x[s] != 0 && (A.stage == 1 || A.uni_u0[s] != 0);
+}
+
 struct CombineCursor {
     int item, c, E, E3, B;
     unsigned mE;
@@ -134,6 +150,8 @@ struct CombineCursor {
         }
         for (; item < n_items; item += gridDim.x) {
             const int s = item / parts, part = item - s * parts;
+            if (uniform_item(A, s))
+                continue;  // done by the uniform pass
             E = A.edge[s];
             E3 = E * E * E;
             B = E + 2 * NG;
@@ -173,7 +191,7 @@ __global__ void __launch_bounds__(COMBINE_THREADS, 1) combine_kernel(CombineArgs
     CombineCursor cur;
     cur.item = blockIdx.x;
     cur.c = -1;
-    bool have = cur.next(A, 1, n_items);
+    bool have = false;
     double xp[MAXNF], lp[MAXNF], vp[MAXNF], xq[MAXNF], lq[MAXNF], vq[MAXNF];
     long long gp = 0, fsp = 0, gq = 0, fsq = 0;
     auto load = [&](double (&xv)[MAXNF], double (&lv)[MAXNF], double (&u0)[MAXNF], long long &g, long long &fs) {
@@ -189,9 +207,75 @@ __global__ void __launch_bounds__(COMBINE_THREADS, 1) combine_kernel(CombineArgs
                     u0[f] = A.U0[g + f * fs];
             }
     };
+    bool fired = false;
+    // uniform pass: the subgrids whose cells all have the same inputs get the
+    // result of one cell, computed by the lanes of warp 0 for 32 of the CTA's
+    // subgrids at a time; where out aliases X or U0 and the result equals the
+    // value already there, nothing is written and the subgrid counts as
+    // unchanged (the ghost fill after this combine then skips subgrids whose
+    // whole neighbourhood is unchanged)
+    __shared__ double s_u[32][MAXNF];
+    __shared__ int s_todo[32];
+    for (int base = blockIdx.x; base < n_items; base += 32 * gridDim.x) {
+        if (threadIdx.x < 32) {
+            const int item = base + (int)threadIdx.x * (int)gridDim.x;
+            int todo = 0;
+            if (item < n_items && uniform_item(A, item)) {
+                const int E = A.edge[item], B = E + 2 * NG;
+                const long long FS = (long long)B * B * B;
+                const long long g0 = A.off[item] + ((long long)NG * B + NG) * B + NG;  // first interior cell
+                double xv[MAXNF], lv[MAXNF], u0[MAXNF], u[MAXNF];
+#pragma unroll
+                for (int f = 0; f < MAXNF; f++)
+                    if (f < nf) {
+                        xv[f] = A.X[g0 + f * FS];
+                        lv[f] = -0.0;
+                        u0[f] = S1 ? 0.0 : A.U0[g0 + f * FS];
+                    }
+                fired |= combine_cell<S1>(A, nf, a, b, dt, xv, lv, u0, u);
+                bool same = false;
+                if (A.out_is_x || A.out_is_u0) {
+                    same = true;
+#pragma unroll
+                    for (int f = 0; f < MAXNF; f++)
+                        if (f < nf)
+                            same &= __double_as_longlong(u[f]) == __double_as_longlong(A.out_is_x ? xv[f] : u0[f]);
+                }
+#pragma unroll
+                for (int f = 0; f < MAXNF; f++)
+                    s_u[threadIdx.x][f] = u[f];
+                todo = same ? 0 : 1;
+                if (A.changed != nullptr)
+                    A.changed[item] = todo;
+            } else if (item < n_items && A.changed != nullptr) {
+                A.changed[item] = 1;  // done cell by cell below
+            }
+            s_todo[threadIdx.x] = todo;
+        }
+        __syncthreads();
+        for (int j = 0; j < 32; j++) {
+            if (!s_todo[j])
+                continue;
+            const int item = base + j * (int)gridDim.x;
+            const int E = A.edge[item], B = E + 2 * NG, E3 = E * E * E;
+            const long long FS = (long long)B * B * B;
+            const unsigned mE = rcp_div(E);
+            for (int c = threadIdx.x; c < E3; c += blockDim.x) {
+                const int zy = div_by(c, mE), z = div_by(zy, mE);
+                const long long gi =
+                    A.off[item] + ((long long)(z + NG) * B + (zy - z * E + NG)) * B + (c - zy * E + NG);
+#pragma unroll
+                for (int f = 0; f < MAXNF; f++)
+                    if (f < nf)
+                        A.out[gi + f * FS] = s_u[j][f];
+            }
+        }
+        __syncthreads();
+    }
+    // the other subgrids cell by cell
+    have = cur.next(A, 1, n_items);
     if (have)
         load(xp, lp, vp, gp, fsp);
-    bool fired = false;
     while (have) {
         // the next cell's loads, then this cell's arithmetic and stores
         const bool more = cur.next(A, 1, n_items);
@@ -264,12 +348,25 @@ struct GhostShell {
 // Ghost cells are enumerated directly (z slabs below and above the interior,
 // then y slabs, then x slabs of the remaining rows); a thread loads all fields
 // of its cell before storing them.
-__global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf, const int *nbr, unsigned *flags)
+// With `changed` (per subgrid: its interior may have changed since U's
+// ghosts were last valid), a subgrid whose own and 26 neighbours' interiors
+// are all unchanged keeps its ghosts as they are.
+__global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf, const int *nbr, unsigned *flags,
+                                  const int *changed)
 {
     const int s = blockIdx.x;
     const int B = E + 2 * NG;
     const long long FS = (long long)B * B * B;
     const int *nb = nbr + 26 * (long long)s;
+    if (changed != nullptr) {
+        int ch = 0;
+        if (threadIdx.x < 27) {
+            const int t = threadIdx.x == 26 ? s : nb[threadIdx.x];
+            ch = t >= 0 && changed[t] != 0;
+        }
+        if (!__syncthreads_or(ch))
+            return;
+    }
     const GhostShell sh(E);
     bool err = false;
     for (int q = threadIdx.x; q < sh.total; q += blockDim.x) {
