@@ -100,6 +100,11 @@ struct oct_hydro {
     int *d_sub_uniform = nullptr;
     int *d_changed = nullptr;  // per subgrid: interior changed by the last combine (stages 2 and 3)
     bool uni_test = false;     // the last RHS launch ran the uniform test
+    // record of the stage state W written by the combines of stages 1 and 2:
+    // per subgrid one value per field (uniform pass) and that value
+    int *d_out_uni = nullptr;
+    double *d_out_val = nullptr;
+    bool ghosts_sourced = false;  // uniform level on which every ghost cell has a source
     long long *d_off = nullptr, *d_doff = nullptr;
     double *d_dx = nullptr;
     WorkItem *d_items = nullptr;
@@ -167,6 +172,8 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_item_begin);
     dfree(h->d_sub_uniform);
     dfree(h->d_changed);
+    dfree(h->d_out_uni);
+    dfree(h->d_out_val);
     dfree(h->d_off);
     dfree(h->d_doff);
     dfree(h->d_dx);
@@ -289,8 +296,12 @@ static oct_status upload_items(oct_hydro *h)
     dfree(h->d_order);
     dfree(h->d_sub_uniform);
     dfree(h->d_changed);
+    dfree(h->d_out_uni);
+    dfree(h->d_out_val);
     CUDA_TRY(cudaMalloc(&h->d_sub_uniform, sizeof(int) * 2 * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_changed, sizeof(int) * std::max(1, h->n_sub)));
+    CUDA_TRY(cudaMalloc(&h->d_out_uni, sizeof(int) * std::max(1, h->n_sub)));
+    CUDA_TRY(cudaMalloc(&h->d_out_val, sizeof(double) * MAXNF * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_items, sizeof(WorkItem) * h->items.size()));
     CUDA_TRY(cudaMemcpy(h->d_items, h->items.data(), sizeof(WorkItem) * h->items.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&h->d_item_begin, sizeof(int) * h->item_begin.size()));
@@ -386,6 +397,34 @@ extern "C" oct_status oct_hydro_create(int n_subgrids, int edge, int ghost, int 
     return OCT_OK;
 }
 
+// Whether every ghost cell of a uniform level has a source: after the
+// zero-gradient clamp along the axes without a face neighbour, the direction
+// left (if any) has a neighbour.
+static bool ghosts_all_sourced(const std::vector<int> &nb, int n)
+{
+    auto slot = [](int dx, int dy, int dz) {
+        const int k = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+        return k > 13 ? k - 1 : k;
+    };
+    for (int t = 0; t < n; t++)
+        for (int k = 0; k < 27; k++) {
+            if (k == 13)
+                continue;
+            const int d[3] = {k % 3 - 1, (k / 3) % 3 - 1, k / 9 - 1};
+            int e[3] = {d[0], d[1], d[2]};
+            for (int a = 0; a < 3; a++)
+                if (d[a] != 0) {
+                    int f[3] = {0, 0, 0};
+                    f[a] = d[a];
+                    if (nb[26 * (size_t)t + slot(f[0], f[1], f[2])] < 0)
+                        e[a] = 0;
+                }
+            if ((e[0] | e[1] | e[2]) != 0 && nb[26 * (size_t)t + slot(e[0], e[1], e[2])] < 0)
+                return false;
+        }
+    return true;
+}
+
 extern "C" oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, const int64_t *offsets,
                                            const double *dx, const int32_t *level, const int32_t *neighbours, int bc)
 {
@@ -448,9 +487,11 @@ extern "C" oct_status oct_hydro_set_layout(oct_hydro_t h, const int32_t *edges, 
             if (nb[i] < -1 || nb[i] >= n)
                 return fail(OCT_E_ARG, "neighbour entry %zu out of range (%d)", i, nb[i]);
     }
+    const bool sourced = bc != OCT_BC_GIVEN && ghosts_all_sourced(nb, n);
     // commit
     free_layout(h);
     h->layout_ok = false;
+    h->ghosts_sourced = sourced;
     h->edge = edge;
     h->dx = dxv;
     h->off = off;
@@ -723,6 +764,7 @@ extern "C" oct_status oct_hydro_set_amr(oct_hydro_t h, const int32_t *level, con
         h->n_corr_cells = (int)first.size() - 1;
     }
     h->bc = OCT_BC_AMR;
+    h->ghosts_sourced = false;
     h->has_prolong = has_prolong;
     h->amr_level.assign(level, level + n);
     h->amr_origin.assign(origin, origin + 3 * (size_t)n);
@@ -822,9 +864,23 @@ static oct_status check_ptr(const void *p, const char *name)
 }
 
 // Launches the RHS kernel of the handle's precision.
+// Whether the stage states of a step can take the whole-subgrid uniform test
+// from the combines' record (uniform level, every ghost sourced, the test on).
+static bool record_test_ok(const oct_hydro *h)
+{
+    return (h->bc == OCT_BC_PERIODIC || h->bc == OCT_BC_OUTFLOW) && h->ghosts_sourced &&
+           h->recon != OCT_RECON_PRIMITIVE;
+}
+
 // uni_slot: which half of the per-subgrid uniform flags the whole-subgrid
 // test writes (1 for the stage states of stages 2 and 3 of a step).
-static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaStream_t st, int uni_slot = 0)
+// uni_mode: 0 the test streams the state and writes the RHS and a_max of the
+// uniform subgrids; 1 (first stage of a step, whose combine takes those
+// subgrids whole without reading their RHS) a_max only; 2 (stages 2 and 3 on
+// a uniform level) the flags from the record of the combine before, nothing
+// written for those subgrids.
+static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaStream_t st, int uni_slot = 0,
+                             int uni_mode = 0)
 {
     RhsArgs A;
     A.U = U;
@@ -860,10 +916,16 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
         return fail(OCT_E_STATE, "work items were cut for another launch shape");
     h->uni_test = h->recon != OCT_RECON_PRIMITIVE && !reflux;
     if (h->uni_test) {
-        // subgrids whose ghosted block is one value per field: RHS and a_max
-        // written here, skipped by the RHS kernel
+        // subgrids whose ghosted block is one value per field: skipped by the
+        // RHS kernel
         int *flags = h->d_sub_uniform + (size_t)uni_slot * h->n_sub;
-        CUDA_TRY(uniform_launch(h->precision, h->n_sub, st, A, h->d_item_begin, flags));
+        if (uni_mode == 2 && record_test_ok(h)) {
+            uniform_from_record_kernel<<<(h->n_sub + 255) / 256, 256, 0, st>>>(h->n_sub, h->nf, h->d_nbr, h->d_out_uni,
+                                                                               h->d_out_val, flags);
+            CUDA_TRY(cudaGetLastError());
+        } else {
+            CUDA_TRY(uniform_launch(h->precision, h->n_sub, st, A, h->d_item_begin, flags, uni_mode == 0));
+        }
         A.sub_uniform = flags;
     }
     int grid = std::min<int>(A.n_items, grid_ctas(h));
@@ -1001,6 +1063,10 @@ static oct_status launch_combine(oct_hydro *h, int stage, const double *U0, cons
     A.changed = stage == 1 ? nullptr : h->d_changed;
     A.out_is_x = out == X;
     A.out_is_u0 = out == U0;
+    // stages 1 and 2 record W for the next stage's uniform test
+    const bool rec = stage <= 2 && h->uni_test && record_test_ok(h);
+    A.out_uni = rec ? h->d_out_uni : nullptr;
+    A.out_val = rec ? h->d_out_val : nullptr;
     // persistent grid over whole subgrids (two cells a thread for edge 8)
     const int n_items = h->n_sub;
     const int grid = std::min(n_items, h->n_sm * h->combine_ctas[stage == 1 ? 1 : 0]);
@@ -1019,17 +1085,17 @@ static oct_status enqueue_step(oct_hydro *h, double *U, cudaStream_t s)
     double *W = h->d_W;
     if (h->bc == OCT_BC_GIVEN)
         CUDA_TRY(cudaMemcpyAsync(W, U, sizeof(double) * h->state_len, cudaMemcpyDeviceToDevice, s));
-    if ((st = launch_rhs(h, U, h->d_L, s)) != OCT_OK) return st;
+    if ((st = launch_rhs(h, U, h->d_L, s, 0, 1)) != OCT_OK) return st;
     if ((st = launch_dt(h, s)) != OCT_OK) return st;
     // the ghost fills after stages 2 and 3 leave alone the subgrids whose
     // neighbourhood the combine did not change (W's ghosts are valid after
     // stage 1's fill, U's on entry)
     if ((st = launch_combine(h, 1, U, U, W, s)) != OCT_OK) return st;
     if ((st = launch_ghosts(h, W, s)) != OCT_OK) return st;
-    if ((st = launch_rhs(h, W, h->d_L, s, 1)) != OCT_OK) return st;
+    if ((st = launch_rhs(h, W, h->d_L, s, 1, 2)) != OCT_OK) return st;
     if ((st = launch_combine(h, 2, U, W, W, s)) != OCT_OK) return st;
     if ((st = launch_ghosts(h, W, s, h->d_changed)) != OCT_OK) return st;
-    if ((st = launch_rhs(h, W, h->d_L, s, 1)) != OCT_OK) return st;
+    if ((st = launch_rhs(h, W, h->d_L, s, 1, 2)) != OCT_OK) return st;
     if ((st = launch_combine(h, 3, U, W, U, s)) != OCT_OK) return st;
     if ((st = launch_ghosts(h, U, s, h->d_changed)) != OCT_OK) return st;
     return OCT_OK;

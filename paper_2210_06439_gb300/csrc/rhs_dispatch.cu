@@ -141,14 +141,14 @@ cudaError_t rhs_launch(int form, int mode, int grid, cudaStream_t stream, const 
 }
 
 cudaError_t uniform_launch(int precision, int n_sub, cudaStream_t stream, const RhsArgs &args, const int *item_begin,
-                           int *sub_uniform)
+                           int *sub_uniform, bool write_rhs)
 {
     if (n_sub <= 0)
         return cudaSuccess;
     if (precision == 0)
-        uniform_subgrid_kernel<double><<<n_sub, UNI_THREADS, 0, stream>>>(args, item_begin, sub_uniform);
+        uniform_subgrid_kernel<double><<<n_sub, UNI_THREADS, 0, stream>>>(args, item_begin, sub_uniform, write_rhs);
     else
-        uniform_subgrid_kernel<float><<<n_sub, UNI_THREADS, 0, stream>>>(args, item_begin, sub_uniform);
+        uniform_subgrid_kernel<float><<<n_sub, UNI_THREADS, 0, stream>>>(args, item_begin, sub_uniform, write_rhs);
     return cudaGetLastError();
 }
 

@@ -1146,9 +1146,11 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
 // (each field one contiguous run of B^3 doubles, read as double2), many CTAs
 // per SM, leaving at the first field that differs.
 constexpr int UNI_THREADS = 256;
+// write_rhs = 0 (inside an RK3 step, whose combines take such subgrids
+// whole and never read their RHS): a_max only.
 template <class T>
 __global__ void __launch_bounds__(UNI_THREADS) uniform_subgrid_kernel(RhsArgs A, const int *item_begin,
-                                                                      int *sub_uniform)
+                                                                      int *sub_uniform, int write_rhs)
 {
     const int s = blockIdx.x, tid = threadIdx.x;
     const int E = A.edge[s], B = E + 2 * NG;
@@ -1187,8 +1189,9 @@ __global__ void __launch_bounds__(UNI_THREADS) uniform_subgrid_kernel(RhsArgs A,
     // the subgrid's RHS: nf E^3 doubles from doff[s] (an even count and offset)
     double2 *d2 = reinterpret_cast<double2 *>(A.dUdt + A.doff[s]);
     const int m2 = nf * E * E * E / 2;
-    for (int q = tid; q < m2; q += UNI_THREADS)
-        d2[q] = make_double2(-0.0, -0.0);
+    if (write_rhs)
+        for (int q = tid; q < m2; q += UNI_THREADS)
+            d2[q] = make_double2(-0.0, -0.0);
     for (int t = item_begin[s] + tid; t < item_begin[s + 1]; t += UNI_THREADS)
         A.amax_tile[t] = amax;
     if (tid == 0) {

@@ -21,6 +21,6 @@ cudaError_t rhs_prepare(int form, int mode, int nf, int *ctas_per_sm);
 cudaError_t rhs_launch(int form, int mode, int grid, cudaStream_t stream, const RhsArgs &args);
 // uniform_subgrid_kernel of a precision (0 FP64, 1 mixed) over n_sub subgrids
 cudaError_t uniform_launch(int precision, int n_sub, cudaStream_t stream, const RhsArgs &args, const int *item_begin,
-                           int *sub_uniform);
+                           int *sub_uniform, bool write_rhs);
 
 }  // namespace octh

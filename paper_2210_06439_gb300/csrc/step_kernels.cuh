@@ -71,6 +71,10 @@ struct CombineArgs {
     const int *uni_x, *uni_u0;
     int *changed;
     int out_is_x, out_is_u0;
+    // optional record of out (null: none): per subgrid whether the uniform
+    // pass gave it one value per field, and that value ([s * MAXNF + f])
+    int *out_uni;
+    double *out_val;
 };
 
 // One SSP-RK3 combine (Shu-Osher) on the interior:
@@ -247,8 +251,19 @@ __global__ void __launch_bounds__(COMBINE_THREADS, 1) combine_kernel(CombineArgs
                 todo = same ? 0 : 1;
                 if (A.changed != nullptr)
                     A.changed[item] = todo;
-            } else if (item < n_items && A.changed != nullptr) {
-                A.changed[item] = 1;  // done cell by cell below
+                if (A.out_uni != nullptr) {
+                    A.out_uni[item] = 1;
+#pragma unroll
+                    for (int f = 0; f < MAXNF; f++)
+                        if (f < nf)
+                            A.out_val[(long long)item * MAXNF + f] = u[f];
+                }
+            } else if (item < n_items) {
+                // done cell by cell below
+                if (A.changed != nullptr)
+                    A.changed[item] = 1;
+                if (A.out_uni != nullptr)
+                    A.out_uni[item] = 0;
             }
             s_todo[threadIdx.x] = todo;
         }
@@ -301,6 +316,31 @@ __global__ void __launch_bounds__(COMBINE_THREADS, 1) combine_kernel(CombineArgs
     }
     if (fired)
         atomicOr(A.flags, 2u);
+}
+
+// The whole-subgrid uniform test of a stage state, derived from the record
+// of the combine that wrote its interiors, right after a uniform-level ghost
+// fill in which every ghost cell has a source: the ghosts of subgrid s copy
+// cells of s itself or of its neighbours, so its ghosted block holds one
+// value per field when s and every neighbour it has took the combine's
+// uniform pass with the same value (bitwise).  A "no" is only conservative.
+__global__ void uniform_from_record_kernel(int n_sub, int nf, const int *nbr, const int *out_uni,
+                                           const double *out_val, int *sub_uniform)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sub)
+        return;
+    int uni = out_uni[s];
+    for (int k = 0; k < 26 && uni; k++) {
+        const int t = nbr[26 * (long long)s + k];
+        if (t < 0)
+            continue;
+        uni = out_uni[t];
+        for (int f = 0; f < nf && uni; f++)
+            uni = __double_as_longlong(out_val[(long long)t * MAXNF + f]) ==
+                  __double_as_longlong(out_val[(long long)s * MAXNF + f]);
+    }
+    sub_uniform[s] = uni;
 }
 
 // The ghost shell of a subgrid of edge E, enumerated as: the two z slabs

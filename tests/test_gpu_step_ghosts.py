@@ -112,10 +112,10 @@ def test_steps_replay_and_match_the_oracle_over_several_steps():
     assert np.array_equal(chk.U, got)
 
 
-def _uniform_box(tau_scale, n_species=5):
-    """A 3x2x2 outflow box of one moving gas state: rho = 1.3, v = (0.2,
-    -0.1, 0.05), p = 0.7, species in fixed fractions, tau = tau_scale *
-    e_int^(1/gamma)."""
+def _uniform_box(tau_scale, periodic=False, n_species=5):
+    """A 3x2x2 box (outflow, or periodic) of one moving gas state: rho = 1.3,
+    v = (0.2, -0.1, 0.05), p = 0.7, species in fixed fractions, tau =
+    tau_scale * e_int^(1/gamma)."""
     g = inputs.GAMMA
     nx, ny, nz, E = 3, 2, 2, 8
     rho, v, p = 1.3, (0.2, -0.1, 0.05), 0.7
@@ -128,12 +128,12 @@ def _uniform_box(tau_scale, n_species=5):
     f[5] = tau_scale * ei ** (1.0 / g)
     for i in range(n_species):
         f[6 + i] = rho * (i + 1) / (n_species * (n_species + 1) / 2)
-    return inputs._tile_global("uniform_box", f, (nx, ny, nz), E, 1.0 / 24, 2, False)
+    return inputs._tile_global("uniform_box", f, (nx, ny, nz), E, 1.0 / 24, 1 if periodic else 2, periodic)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("tau_scale", [1.0, 0.5])
-def test_uniform_box_steps(precision, tau_scale):
+@pytest.mark.parametrize("tau_scale,periodic", [(1.0, False), (0.5, False), (0.5, True)])
+def test_uniform_box_steps(precision, tau_scale, periodic):
     """Every subgrid holds one state, so every RHS is -0.0 and the combines
     take their per-subgrid pass: with tau = e_int^(1/gamma) the state is a
     fixed point of the step to within the re-synchronisation's rounding (the
@@ -144,7 +144,7 @@ def test_uniform_box_steps(precision, tau_scale):
     and the ghosts exactly the oracle's ghost fill of the interior."""
     import torch
     from paper_2210_06439_gb300 import binding
-    p = _uniform_box(tau_scale)
+    p = _uniform_box(tau_scale, periodic)
     ref = oracle_filled(p)
     U = torch.from_numpy(ref.U.copy()).cuda()
     H = binding.Hydro.from_problem(p, precision=precision)
@@ -191,3 +191,30 @@ def test_binary_star_steps(precision):
     chk.U[:] = got
     oracle.ghost_fill(8, chk.off, chk.nf, chk.nbr, chk.U)
     assert np.array_equal(chk.U, got)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uniform_box_steps_with_given_ghosts(precision):
+    """The uniform box with its ghosts given (filled once, never refilled):
+    the step's stage states carry the given ghosts, so their uniform test
+    streams the blocks instead of reading the combines' record.  Three
+    steps against the oracle's, the ghosts left as they were."""
+    import torch
+    from paper_2210_06439_gb300 import binding
+    p = oracle_filled(_uniform_box(0.5))
+    p.bc = 0
+    ref = p.copy()
+    U = torch.from_numpy(p.U.copy()).cuda()
+    H = binding.Hydro.from_problem(p, precision=precision)
+    for _ in range(3):
+        dt_o, _, st = oracle.rk3_step(ref.edge, ref.off, ref.dx, ref.nf, ref.U, bc=0)
+        assert st == 0
+        dt_g = H.rk_step(U)
+        assert dt_g == pytest.approx(dt_o, rel=1e-12 if precision == 0 else 2e-6)
+    got = U.cpu().numpy()
+    errs = field_errors(interior_layout(got, p), interior_layout(ref.U, p), p.nf, e3s(p))
+    assert np.all(errs <= (1e-12 if precision == 0 else 1e-6)), errs
+    ghosts = interior_layout(np.arange(got.size, dtype=np.float64), p)  # interior indices
+    mask = np.ones(got.size, bool)
+    mask[ghosts.astype(np.int64)] = False
+    assert np.array_equal(got[mask], p.U[mask])
