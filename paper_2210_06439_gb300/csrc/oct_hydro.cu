@@ -301,6 +301,7 @@ static oct_status upload_items(oct_hydro *h)
     CUDA_TRY(cudaMalloc(&h->d_sub_uniform, sizeof(int) * 2 * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_changed, sizeof(int) * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_out_uni, sizeof(int) * std::max(1, h->n_sub)));
+    CUDA_TRY(cudaMemset(h->d_out_uni, 0, sizeof(int) * std::max(1, h->n_sub)));  // W holds nothing known
     CUDA_TRY(cudaMalloc(&h->d_out_val, sizeof(double) * MAXNF * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_items, sizeof(WorkItem) * h->items.size()));
     CUDA_TRY(cudaMemcpy(h->d_items, h->items.data(), sizeof(WorkItem) * h->items.size(), cudaMemcpyHostToDevice));
@@ -872,6 +873,12 @@ static bool record_test_ok(const oct_hydro *h)
            h->recon != OCT_RECON_PRIMITIVE;
 }
 
+// Whether the combines keep the record of W (uniform test on, record test
+// possible).  W belongs to the handle and only the step writes it, so the
+// record that stage 2 leaves describes W at the next step's start; a step
+// without the record clears it (enqueue_step), as does a new layout.
+static bool w_record_ok(const oct_hydro *h) { return h->uni_test && record_test_ok(h); }
+
 // uni_slot: which half of the per-subgrid uniform flags the whole-subgrid
 // test writes (1 for the stage states of stages 2 and 3 of a step).
 // uni_mode: 0 the test streams the state and writes the RHS and a_max of the
@@ -1060,13 +1067,14 @@ static oct_status launch_combine(oct_hydro *h, int stage, const double *U0, cons
     // 3: the stage state, and U as of stage 1), when the RHS ran that test
     A.uni_u0 = h->uni_test ? h->d_sub_uniform : nullptr;
     A.uni_x = h->uni_test ? h->d_sub_uniform + (stage == 1 ? 0 : h->n_sub) : nullptr;
-    A.changed = stage == 1 ? nullptr : h->d_changed;
     A.out_is_x = out == X;
     A.out_is_u0 = out == U0;
-    // stages 1 and 2 record W for the next stage's uniform test
-    const bool rec = stage <= 2 && h->uni_test && record_test_ok(h);
+    // stages 1 and 2 record W for the next stage's uniform test; stage 1
+    // also compares with the record of W that the last step left
+    const bool rec = stage <= 2 && w_record_ok(h);
     A.out_uni = rec ? h->d_out_uni : nullptr;
     A.out_val = rec ? h->d_out_val : nullptr;
+    A.changed = stage == 1 && !rec ? nullptr : h->d_changed;
     // persistent grid over whole subgrids (two cells a thread for edge 8)
     const int n_items = h->n_sub;
     const int grid = std::min(n_items, h->n_sm * h->combine_ctas[stage == 1 ? 1 : 0]);
@@ -1087,11 +1095,13 @@ static oct_status enqueue_step(oct_hydro *h, double *U, cudaStream_t s)
         CUDA_TRY(cudaMemcpyAsync(W, U, sizeof(double) * h->state_len, cudaMemcpyDeviceToDevice, s));
     if ((st = launch_rhs(h, U, h->d_L, s, 0, 1)) != OCT_OK) return st;
     if ((st = launch_dt(h, s)) != OCT_OK) return st;
-    // the ghost fills after stages 2 and 3 leave alone the subgrids whose
-    // neighbourhood the combine did not change (W's ghosts are valid after
-    // stage 1's fill, U's on entry)
+    // the ghost fills leave alone the subgrids whose neighbourhood the
+    // combine before did not change: W's ghosts are valid after the last
+    // step's stage 2 (and after stage 1's fill), U's on entry
+    if (!w_record_ok(h))
+        CUDA_TRY(cudaMemsetAsync(h->d_out_uni, 0, sizeof(int) * std::max(1, h->n_sub), s));
     if ((st = launch_combine(h, 1, U, U, W, s)) != OCT_OK) return st;
-    if ((st = launch_ghosts(h, W, s)) != OCT_OK) return st;
+    if ((st = launch_ghosts(h, W, s, w_record_ok(h) ? h->d_changed : nullptr)) != OCT_OK) return st;
     if ((st = launch_rhs(h, W, h->d_L, s, 1, 2)) != OCT_OK) return st;
     if ((st = launch_combine(h, 2, U, W, W, s)) != OCT_OK) return st;
     if ((st = launch_ghosts(h, W, s, h->d_changed)) != OCT_OK) return st;

@@ -72,7 +72,8 @@ struct CombineArgs {
     int *changed;
     int out_is_x, out_is_u0;
     // optional record of out (null: none): per subgrid whether the uniform
-    // pass gave it one value per field, and that value ([s * MAXNF + f])
+    // pass gave it one value per field, and that value ([s * MAXNF + f]).
+    // In stage 1 it describes out (W) as left by the last step, on entry.
     int *out_uni;
     double *out_val;
 };
@@ -244,6 +245,15 @@ __global__ void __launch_bounds__(COMBINE_THREADS, 1) combine_kernel(CombineArgs
                     for (int f = 0; f < MAXNF; f++)
                         if (f < nf)
                             same &= __double_as_longlong(u[f]) == __double_as_longlong(A.out_is_x ? xv[f] : u0[f]);
+                } else if (A.out_uni != nullptr && A.out_uni[item] != 0) {
+                    // stage 1: out (W) still holds what the last combine that
+                    // wrote it recorded
+                    same = true;
+#pragma unroll
+                    for (int f = 0; f < MAXNF; f++)
+                        if (f < nf)
+                            same &= __double_as_longlong(u[f]) ==
+                                    __double_as_longlong(A.out_val[(long long)item * MAXNF + f]);
                 }
 #pragma unroll
                 for (int f = 0; f < MAXNF; f++)

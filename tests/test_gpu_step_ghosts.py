@@ -218,3 +218,37 @@ def test_uniform_box_steps_with_given_ghosts(precision):
     mask = np.ones(got.size, bool)
     mask[ghosts.astype(np.int64)] = False
     assert np.array_equal(got[mask], p.U[mask])
+
+
+def test_two_states_alternating_on_one_handle():
+    """The handle's stage state W is shared by every state it steps, and its
+    first combine compares with what the last step left there.  Two uniform
+    boxes of the same layout and different values (the second with tau
+    consistent and density, momenta, energy and species doubled), stepped
+    in turn, twice each, each step against the oracle's; ghosts bitwise."""
+    import torch
+    from paper_2210_06439_gb300 import binding
+    pa = _uniform_box(0.5)
+    pb = _uniform_box(1.0)
+    for s in range(pb.n_sub):
+        b = pb.block(s)
+        b[0] *= 2.0
+        b[1:5] *= 2.0
+        b[6:] *= 2.0
+    refs = [oracle_filled(pa), oracle_filled(pb)]
+    Us = [torch.from_numpy(r.U.copy()).cuda() for r in refs]
+    H = binding.Hydro.from_problem(pa)
+    for k in range(4):
+        i = k % 2
+        ref = refs[i]
+        dt_o, _, st = oracle.rk3_step(ref.edge, ref.off, ref.dx, ref.nf, ref.U, bc=ref.bc, nbr=ref.nbr)
+        assert st == 0
+        dt_g = H.rk_step(Us[i])
+        assert dt_g == pytest.approx(dt_o, rel=1e-12)
+        got = Us[i].cpu().numpy()
+        errs = field_errors(interior_layout(got, pa), interior_layout(ref.U, pa), pa.nf, e3s(pa))
+        assert np.all(errs <= 1e-12), (k, errs)
+        chk = pa.copy()
+        chk.U[:] = got
+        oracle.ghost_fill(8, chk.off, chk.nf, chk.nbr, chk.U)
+        assert np.array_equal(chk.U, got), k
