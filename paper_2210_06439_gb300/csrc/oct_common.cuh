@@ -69,6 +69,13 @@ struct RhsArgs {
     // per subgrid: 1 when its ghosted block holds one value per field and
     // uniform_subgrid_kernel has written its RHS and a_max (null: no such test)
     const int *sub_uniform;
+    // optional (null: the static items): the items of the subgrids left
+    // after the uniform test, n_live[0] of them, and per item the slot of
+    // amax_tile it reports to (~slot: half of a static item, reported by
+    // atomic max into a slot zeroed beforehand)
+    const WorkItem *live_items;
+    const int *live_slot;
+    const int *n_live;
 };
 
 // q / d for the small divisors of the kernels' index arithmetic (tile widths,

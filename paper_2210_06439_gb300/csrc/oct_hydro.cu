@@ -104,6 +104,13 @@ struct oct_hydro {
     // per subgrid one value per field (uniform pass) and that value
     int *d_out_uni = nullptr;
     double *d_out_val = nullptr;
+    // record of the interiors of the state a step starts from (first stage)
+    int *d_u_uni = nullptr;
+    double *d_u_val = nullptr;
+    // the RHS launch's work list after the uniform test (live_items_kernel)
+    WorkItem *d_live_items = nullptr;
+    int *d_live_slot = nullptr, *d_n_live = nullptr;
+    bool items_live_split = false;
     bool ghosts_sourced = false;  // uniform level on which every ghost cell has a source
     long long *d_off = nullptr, *d_doff = nullptr;
     double *d_dx = nullptr;
@@ -174,6 +181,11 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_changed);
     dfree(h->d_out_uni);
     dfree(h->d_out_val);
+    dfree(h->d_u_uni);
+    dfree(h->d_u_val);
+    dfree(h->d_live_items);
+    dfree(h->d_live_slot);
+    dfree(h->d_n_live);
     dfree(h->d_off);
     dfree(h->d_doff);
     dfree(h->d_dx);
@@ -252,6 +264,9 @@ static void build_items(oct_hydro *h)
     const int ty0 = (h->tile_mode == 1) ? 4 : (h->edge[0] == 12 ? 6 : 8);
     const long long r = n_tiles % G;
     const long long split_from = (same && r > 0 && 2 * r <= G && ty0 % 2 == 0) ? n_tiles - r : n_tiles;
+    // the work list after the uniform test may cut its own last round in
+    // half when the static items are all whole tiles of an even height >= 4
+    h->items_live_split = same && split_from == n_tiles && ty0 % 2 == 0 && ty0 >= 4;
     long long k = 0;
     for (int s = 0; s < h->n_sub; s++) {
         h->item_begin[s] = (int)h->items.size();
@@ -298,11 +313,21 @@ static oct_status upload_items(oct_hydro *h)
     dfree(h->d_changed);
     dfree(h->d_out_uni);
     dfree(h->d_out_val);
+    dfree(h->d_u_uni);
+    dfree(h->d_u_val);
+    dfree(h->d_live_items);
+    dfree(h->d_live_slot);
+    dfree(h->d_n_live);
     CUDA_TRY(cudaMalloc(&h->d_sub_uniform, sizeof(int) * 2 * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_changed, sizeof(int) * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_out_uni, sizeof(int) * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMemset(h->d_out_uni, 0, sizeof(int) * std::max(1, h->n_sub)));  // W holds nothing known
     CUDA_TRY(cudaMalloc(&h->d_out_val, sizeof(double) * MAXNF * std::max(1, h->n_sub)));
+    CUDA_TRY(cudaMalloc(&h->d_live_items, sizeof(WorkItem) * 2 * std::max<size_t>(1, h->items.size())));
+    CUDA_TRY(cudaMalloc(&h->d_live_slot, sizeof(int) * 2 * std::max<size_t>(1, h->items.size())));
+    CUDA_TRY(cudaMalloc(&h->d_n_live, sizeof(int)));
+    CUDA_TRY(cudaMalloc(&h->d_u_uni, sizeof(int) * std::max(1, h->n_sub)));
+    CUDA_TRY(cudaMalloc(&h->d_u_val, sizeof(double) * MAXNF * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_items, sizeof(WorkItem) * h->items.size()));
     CUDA_TRY(cudaMemcpy(h->d_items, h->items.data(), sizeof(WorkItem) * h->items.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&h->d_item_begin, sizeof(int) * h->item_begin.size()));
@@ -873,6 +898,14 @@ static bool record_test_ok(const oct_hydro *h)
            h->recon != OCT_RECON_PRIMITIVE;
 }
 
+// Whether an RHS launch takes its work list from live_items_kernel after the
+// uniform test: one edge (no execution order), 8 or 16.
+static bool live_ok(const oct_hydro *h)
+{
+    return h->recon != OCT_RECON_PRIMITIVE && !(h->bc == OCT_BC_AMR && h->n_corr_cells > 0) && h->order.empty() &&
+           !h->edge.empty() && (h->edge[0] == 8 || h->edge[0] == 16);
+}
+
 // Whether the combines keep the record of W (uniform test on, record test
 // possible).  W belongs to the handle and only the step writes it, so the
 // record that stage 2 leaves describes W at the next step's start; a step
@@ -883,9 +916,11 @@ static bool w_record_ok(const oct_hydro *h) { return h->uni_test && record_test_
 // test writes (1 for the stage states of stages 2 and 3 of a step).
 // uni_mode: 0 the test streams the state and writes the RHS and a_max of the
 // uniform subgrids; 1 (first stage of a step, whose combine takes those
-// subgrids whole without reading their RHS) a_max only; 2 (stages 2 and 3 on
-// a uniform level) the flags from the record of the combine before, nothing
-// written for those subgrids.
+// subgrids whole without reading their RHS) a_max only -- on a uniform level
+// whose ghosts all have a source, from the interiors alone, since the state
+// a step starts from has valid ghosts; 2 (stages 2 and 3 on a uniform
+// level) the flags from the record of the combine before, nothing written
+// for those subgrids.
 static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaStream_t st, int uni_slot = 0,
                              int uni_mode = 0)
 {
@@ -927,15 +962,33 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
         // RHS kernel
         int *flags = h->d_sub_uniform + (size_t)uni_slot * h->n_sub;
         if (uni_mode == 2 && record_test_ok(h)) {
-            uniform_from_record_kernel<<<(h->n_sub + 255) / 256, 256, 0, st>>>(h->n_sub, h->nf, h->d_nbr, h->d_out_uni,
-                                                                               h->d_out_val, flags);
-            CUDA_TRY(cudaGetLastError());
+            // "yes" from the record; the other subgrids streamed
+            CUDA_TRY(record_test_launch(h->precision, h->n_sub, st, A, h->d_nbr, h->d_out_uni, h->d_out_val, flags,
+                                        nullptr));
+            CUDA_TRY(uniform_launch(h->precision, h->n_sub, st, A, h->d_item_begin, flags, false, true));
+        } else if (uni_mode == 1 && record_test_ok(h)) {
+            CUDA_TRY(interior_record_launch(h->n_sub, st, A, h->d_u_uni, h->d_u_val));
+            CUDA_TRY(record_test_launch(h->precision, h->n_sub, st, A, h->d_nbr, h->d_u_uni, h->d_u_val, flags,
+                                        h->d_item_begin));
+            CUDA_TRY(uniform_launch(h->precision, h->n_sub, st, A, h->d_item_begin, flags, false, true));
         } else {
             CUDA_TRY(uniform_launch(h->precision, h->n_sub, st, A, h->d_item_begin, flags, uni_mode == 0));
         }
         A.sub_uniform = flags;
     }
+    A.live_items = nullptr;
+    A.live_slot = nullptr;
+    A.n_live = nullptr;
     int grid = std::min<int>(A.n_items, grid_ctas(h));
+    if (h->uni_test && live_ok(h)) {
+        // the items of the subgrids left, the last round cut in half when at
+        // most half full
+        CUDA_TRY(live_items_launch(h->n_sub, st, A.sub_uniform, h->d_item_begin, h->d_items, grid, h->items_live_split,
+                                   h->d_live_items, h->d_live_slot, h->d_n_live, h->d_amax_tile));
+        A.live_items = h->d_live_items;
+        A.live_slot = h->d_live_slot;
+        A.n_live = h->d_n_live;
+    }
     CUDA_TRY(rhs_launch(form, mode, grid, st, A));
     CUDA_TRY(cudaGetLastError());
     if (reflux) {
@@ -1111,21 +1164,31 @@ static oct_status enqueue_step(oct_hydro *h, double *U, cudaStream_t s)
     return OCT_OK;
 }
 
+// Ghost-fill launches per stage.
+static int per_fill_of(const oct_hydro *h)
+{
+    if (h->bc == OCT_BC_AMR)
+        return h->has_prolong ? 2 : 1;
+    return h->bc != OCT_BC_GIVEN ? 1 : 0;
+}
+
 extern "C" int oct_hydro_step_launches(oct_hydro_t h)
 {
     if (!h || !h->layout_ok)
         return -1;
     const bool reflux = h->bc == OCT_BC_AMR && h->n_corr_cells > 0;
-    // the RHS kernel, with the primitive pass before it (primitive
-    // reconstruction) or else the whole-subgrid uniform test, and the flux
-    // correction after it across levels
-    int per_rhs = 1 + (h->recon == OCT_RECON_PRIMITIVE ? 1 : (reflux ? 0 : 1)) + (reflux ? 1 : 0);
-    int per_fill = 0;
-    if (h->bc == OCT_BC_AMR)
-        per_fill = h->has_prolong ? 2 : 1;
-    else if (h->bc != OCT_BC_GIVEN)
-        per_fill = 1;
-    return 3 * per_rhs + 1 + 3 + 3 * per_fill;
+    // per stage the RHS kernel, with the primitive pass before it (primitive
+    // reconstruction) or else the whole-subgrid uniform test and the work
+    // list after it, and the flux correction after it across levels; the
+    // uniform test is one streaming kernel, or on a uniform level whose
+    // ghosts all have a source three (first stage: the interiors' record, the
+    // test from it, the stream over the rest) and two (later stages: the test
+    // from the combine's record, the stream over the rest)
+    const bool uni = h->recon != OCT_RECON_PRIMITIVE && !reflux;
+    const bool rec = uni && (h->bc == OCT_BC_PERIODIC || h->bc == OCT_BC_OUTFLOW) && h->ghosts_sourced;
+    const int tests = uni ? (rec ? 3 + 2 + 2 : 3) : 0;
+    const int extra = h->recon == OCT_RECON_PRIMITIVE ? 3 : (reflux ? 3 : 0);
+    return 3 + tests + extra + (uni && live_ok(h) ? 3 : 0) + 1 + 3 + 3 * per_fill_of(h);
 }
 
 extern "C" oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_used_host_out, void *cuda_stream)
@@ -1645,6 +1708,9 @@ extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_s
     A.order = nullptr;
     A.ticket = nullptr;
     A.sub_uniform = nullptr;  // the kernel's own per-item uniform test
+    A.live_items = nullptr;
+    A.live_slot = nullptr;
+    A.n_live = nullptr;
     int grid = std::min(n_items, D->n_sm * D->ctas[precision]);
     CUDA_TRY(rhs_launch(precision, 0, grid, s, A));
     dt_kernel<<<1, 1024, 0, s>>>(n_items, d_items, dx, d_amax, cfl, nullptr, dt);

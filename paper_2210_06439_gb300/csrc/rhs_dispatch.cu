@@ -141,14 +141,51 @@ cudaError_t rhs_launch(int form, int mode, int grid, cudaStream_t stream, const 
 }
 
 cudaError_t uniform_launch(int precision, int n_sub, cudaStream_t stream, const RhsArgs &args, const int *item_begin,
-                           int *sub_uniform, bool write_rhs)
+                           int *sub_uniform, bool write_rhs, bool only_unknown)
 {
     if (n_sub <= 0)
         return cudaSuccess;
     if (precision == 0)
-        uniform_subgrid_kernel<double><<<n_sub, UNI_THREADS, 0, stream>>>(args, item_begin, sub_uniform, write_rhs);
+        uniform_subgrid_kernel<double><<<n_sub, UNI_THREADS, 0, stream>>>(args, item_begin, sub_uniform, write_rhs,
+                                                                          only_unknown);
     else
-        uniform_subgrid_kernel<float><<<n_sub, UNI_THREADS, 0, stream>>>(args, item_begin, sub_uniform, write_rhs);
+        uniform_subgrid_kernel<float><<<n_sub, UNI_THREADS, 0, stream>>>(args, item_begin, sub_uniform, write_rhs,
+                                                                         only_unknown);
+    return cudaGetLastError();
+}
+
+cudaError_t live_items_launch(int n_sub, cudaStream_t stream, const int *sub_uniform, const int *item_begin,
+                              const WorkItem *items, int grid, bool split, WorkItem *live, int *live_slot,
+                              int *n_live, double *amax_tile)
+{
+    live_items_kernel<<<1, LIVE_THREADS, 0, stream>>>(n_sub, sub_uniform, item_begin, items, grid, split ? 1 : 0,
+                                                      live, live_slot, n_live, amax_tile);
+    return cudaGetLastError();
+}
+
+cudaError_t interior_record_launch(int n_sub, cudaStream_t stream, const RhsArgs &args, int *rec_uni,
+                                   double *rec_val)
+{
+    if (n_sub <= 0)
+        return cudaSuccess;
+    constexpr int per = REC_THREADS / 32;  // one warp per subgrid
+    interior_record_kernel<<<(n_sub + per - 1) / per, REC_THREADS, 0, stream>>>(args.U, args.edge, args.off, args.nf,
+                                                                                 n_sub, rec_uni, rec_val);
+    return cudaGetLastError();
+}
+
+cudaError_t record_test_launch(int precision, int n_sub, cudaStream_t stream, const RhsArgs &args, const int *nbr,
+                               const int *rec_uni, const double *rec_val, int *sub_uniform, const int *item_begin)
+{
+    if (n_sub <= 0)
+        return cudaSuccess;
+    const int grid = (n_sub + 255) / 256;
+    if (precision == 0)
+        uniform_from_record_kernel<double><<<grid, 256, 0, stream>>>(args, n_sub, nbr, rec_uni, rec_val, sub_uniform,
+                                                                      item_begin);
+    else
+        uniform_from_record_kernel<float><<<grid, 256, 0, stream>>>(args, n_sub, nbr, rec_uni, rec_val, sub_uniform,
+                                                                     item_begin);
     return cudaGetLastError();
 }
 

@@ -528,9 +528,10 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
     __shared__ int s_const[2];
     if (tid < 2)
         s_const[tid] = 0;
-    for (int k = blockIdx.x; k < A.n_items;) {
-        const int it = A.order != nullptr ? A.order[k] : k;
-        const WorkItem W = A.items[it];
+    const int n_items = A.n_live != nullptr ? A.n_live[0] : A.n_items;
+    for (int k = blockIdx.x; k < n_items;) {
+        const int it = A.n_live != nullptr ? k : (A.order != nullptr ? A.order[k] : k);
+        const WorkItem W = A.n_live != nullptr ? A.live_items[k] : A.items[it];
         const int s = W.s, x0 = W.x0, y0 = W.y0, tx = W.txty & 0xFF, ty = (W.txty >> 8) & 0xFF;
         if (A.sub_uniform != nullptr && A.sub_uniform[s] != 0) {
             // the subgrid's whole ghosted block holds one value per field: its
@@ -1115,7 +1116,12 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
             double m = 0.0;
             for (int w = 0; w < NT / 32; w++)
                 m = fmax(m, red[w]);
-            A.amax_tile[it] = m;
+            const int slot = A.n_live != nullptr ? A.live_slot[k] : it;
+            if (slot >= 0)
+                A.amax_tile[slot] = m;
+            else  // half of a static item: non-negative doubles order as their bits
+                atomicMax(reinterpret_cast<unsigned long long *>(A.amax_tile + ~slot),
+                          (unsigned long long)__double_as_longlong(m));
             s_next[par] = A.ticket != nullptr ? (int)gridDim.x + atomicAdd(A.ticket, 1) : k + (int)gridDim.x;
         }
         __syncthreads();
@@ -1147,12 +1153,16 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
 // per SM, leaving at the first field that differs.
 constexpr int UNI_THREADS = 256;
 // write_rhs = 0 (inside an RK3 step, whose combines take such subgrids
-// whole and never read their RHS): a_max only.
+// whole and never read their RHS): a_max only.  only_unknown: the subgrids
+// already marked uniform (by the test from a record) are left as they are.
 template <class T>
 __global__ void __launch_bounds__(UNI_THREADS) uniform_subgrid_kernel(RhsArgs A, const int *item_begin,
-                                                                      int *sub_uniform, int write_rhs)
+                                                                      int *sub_uniform, int write_rhs,
+                                                                      int only_unknown)
 {
     const int s = blockIdx.x, tid = threadIdx.x;
+    if (only_unknown && sub_uniform[s] == 1)
+        return;
     const int E = A.edge[s], B = E + 2 * NG;
     const int n2 = B * B * B / 2;  // B is even: whole double2 per field
     const double *Ub = A.U + A.off[s];
@@ -1199,6 +1209,177 @@ __global__ void __launch_bounds__(UNI_THREADS) uniform_subgrid_kernel(RhsArgs A,
         if (bad)
             atomicOr(A.flags, 1u);
     }
+}
+
+// The work list of an RHS launch after the uniform test, on a batch of one
+// edge: the static items of the subgrids not found uniform, in subgrid
+// order, and -- as the static list does for its own last round -- when the
+// last round of the persistent grid (G CTAs) would be at most half full,
+// its r items cut in half along y (split: the static items are whole tiles
+// of an even height of at least 4, so the halves are at least 2 high).  One CTA of LIVE_THREADS threads: each scans a contiguous run of
+// subgrids, a block scan gives the positions.  Also zeroes the a_max slots
+// that halves report to by atomic max.
+constexpr int LIVE_THREADS = 1024;
+static __global__ void __launch_bounds__(LIVE_THREADS) live_items_kernel(int n_sub, const int *sub_uniform,
+                                                                  const int *item_begin, const WorkItem *items,
+                                                                  int G, int split, WorkItem *live, int *live_slot,
+                                                                  int *n_live, double *amax_tile)
+{
+    __shared__ int wsum[LIVE_THREADS / 32];
+    __shared__ int s_total;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int per = (n_sub + LIVE_THREADS - 1) / LIVE_THREADS;
+    const int s0 = min(n_sub, tid * per), s1 = min(n_sub, s0 + per);
+    int cnt = 0;
+    for (int s = s0; s < s1; s++)
+        if (!sub_uniform[s])
+            cnt += item_begin[s + 1] - item_begin[s];
+    // exclusive scan of cnt over the block
+    int x = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int v = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+            if (lane >= o)
+                v += y;
+        }
+        wsum[lane] = v;  // inclusive over warps
+        if (lane == 31)
+            s_total = v;
+    }
+    __syncthreads();
+    int j = x - cnt + (w > 0 ? wsum[w - 1] : 0);  // first live item of this thread
+    const int N = s_total;
+    const int r = N % G;
+    const int cut_from = (split && r > 0 && 2 * r <= G) ? N - r : N;
+    for (int s = s0; s < s1; s++) {
+        if (sub_uniform[s])
+            continue;
+        for (int i = item_begin[s]; i < item_begin[s + 1]; i++, j++) {
+            const WorkItem it = items[i];
+            if (j < cut_from) {
+                live[j] = it;
+                live_slot[j] = i;
+            } else {
+                const int ty = (it.txty >> 8) & 0xFF, tx = it.txty & 0xFF, h2 = ty / 2;
+                const int p = cut_from + 2 * (j - cut_from);
+                WorkItem a = it, b = it;
+                a.txty = tx | (h2 << 8);
+                b.y0 = it.y0 + h2;
+                b.txty = tx | ((ty - h2) << 8);
+                live[p] = a;
+                live[p + 1] = b;
+                live_slot[p] = ~i;
+                live_slot[p + 1] = ~i;
+                amax_tile[i] = 0.0;
+            }
+        }
+    }
+    if (tid == 0)
+        n_live[0] = cut_from + 2 * (N - cut_from);
+}
+
+// Interior test of a state whose ghost cells are valid copies of interior
+// cells (the state an RK3 step starts from, by the ABI's contract): per
+// subgrid whether its interior holds one value per field (bitwise), and
+// that value ([s * MAXNF + f]).  One warp per subgrid, no block barrier:
+// each lane loads all fields of two cells at a time (22 loads in flight for
+// 11 fields), the warp votes after each pair of cells.
+constexpr int REC_THREADS = 256;
+static __global__ void __launch_bounds__(REC_THREADS) interior_record_kernel(const double *U, const int *edge,
+                                                                             const long long *off, int nf,
+                                                                             int n_sub, int *rec_uni,
+                                                                             double *rec_val)
+{
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (REC_THREADS / 32) + (threadIdx.x >> 5);
+    if (s >= n_sub)
+        return;
+    const int E = edge[s], B = E + 2 * NG, E3 = E * E * E;
+    const long long FS = (long long)B * B * B;
+    const double *U0 = U + off[s] + ((long long)NG * B + NG) * B + NG;  // first interior cell
+    const unsigned mE = rcp_div(E);
+    double ref[MAXNF];
+#pragma unroll
+    for (int f = 0; f < MAXNF; f++)
+        ref[f] = f < nf ? __ldg(U0 + f * FS) : 0.0;
+    bool diff = false;
+    for (int c0 = 0; c0 < E3 && !diff; c0 += 64) {
+        unsigned d = 0;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int c = c0 + 32 * h + lane;
+            if (c < E3) {
+                const int zy = div_by(c, mE), z = div_by(zy, mE);
+                const long long o = ((long long)z * B + (zy - z * E)) * B + (c - zy * E);
+#pragma unroll
+                for (int f = 0; f < MAXNF; f++)
+                    if (f < nf)
+                        d |= bit_diff(__ldg(U0 + f * FS + o), ref[f]);
+            }
+        }
+        diff = __any_sync(0xFFFFFFFFu, d != 0u);
+    }
+    if (lane == 0)
+        rec_uni[s] = !diff;
+    if (!diff && lane < nf)
+        rec_val[(long long)s * MAXNF + lane] = ref[lane];
+}
+
+// The whole-subgrid uniform test from a per-subgrid record of interiors (the
+// interior test above, or the record the combines keep of the stage state),
+// on a uniform level whose ghost cells are valid copies and all have a
+// source: the ghosts of subgrid s copy cells of s itself or of its
+// neighbours, so its ghosted block holds one value per field when s and
+// every neighbour it has hold the same value (bitwise); a "no" is only
+// conservative.  With item_begin (the first stage of a step, whose dt needs
+// them), a_max of each uniform subgrid's items as the RHS kernel's uniform
+// path would give it, in the form's precision.  One thread per subgrid.
+template <class T>
+__global__ void uniform_from_record_kernel(RhsArgs A, int n_sub, const int *nbr, const int *rec_uni,
+                                           const double *rec_val, int *sub_uniform, const int *item_begin)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sub)
+        return;
+    const int nf = A.nf;
+    int uni = rec_uni[s];
+    for (int k = 0; k < 26 && uni; k++) {
+        const int t = nbr[26 * (long long)s + k];
+        if (t < 0)
+            continue;
+        uni = rec_uni[t];
+        for (int f = 0; f < nf && uni; f++)
+            uni = __double_as_longlong(rec_val[(long long)t * MAXNF + f]) ==
+                  __double_as_longlong(rec_val[(long long)s * MAXNF + f]);
+    }
+    sub_uniform[s] = uni;
+    if (!uni || item_begin == nullptr)
+        return;
+    const T gamma = Num<T>::from_d(A.gamma);
+    const T gm1 = Num<T>::from_d(A.gamma - 1.0);
+    const T ggm1 = Num<T>::from_d(A.gamma * (A.gamma - 1.0));
+    const T eps1 = Num<T>::from_d(A.eps1);
+    T qh[6], v[3], p, c;
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+        qh[f] = Num<T>::from_d(rec_val[(long long)s * MAXNF + f]);
+    bool bad = false;
+    prim_point(qh, gamma, gm1, ggm1, eps1, v, p, c, bad);
+    const T a = max_nonneg(max_nonneg(fabs(v[0]) + c, fabs(v[1]) + c), fabs(v[2]) + c);
+    const double amax = Num<T>::to_d(a);
+    for (int t = item_begin[s]; t < item_begin[s + 1]; t++)
+        A.amax_tile[t] = amax;
+    if (bad)
+        atomicOr(A.flags, 1u);
 }
 
 }  // namespace octh

@@ -21,6 +21,16 @@ cudaError_t rhs_prepare(int form, int mode, int nf, int *ctas_per_sm);
 cudaError_t rhs_launch(int form, int mode, int grid, cudaStream_t stream, const RhsArgs &args);
 // uniform_subgrid_kernel of a precision (0 FP64, 1 mixed) over n_sub subgrids
 cudaError_t uniform_launch(int precision, int n_sub, cudaStream_t stream, const RhsArgs &args, const int *item_begin,
-                           int *sub_uniform, bool write_rhs);
+                           int *sub_uniform, bool write_rhs, bool only_unknown = false);
+// live_items_kernel (one CTA)
+cudaError_t live_items_launch(int n_sub, cudaStream_t stream, const int *sub_uniform, const int *item_begin,
+                              const WorkItem *items, int grid, bool split, WorkItem *live, int *live_slot,
+                              int *n_live, double *amax_tile);
+// interior_record_kernel over n_sub subgrids of args.U
+cudaError_t interior_record_launch(int n_sub, cudaStream_t stream, const RhsArgs &args, int *rec_uni,
+                                   double *rec_val);
+// uniform_from_record_kernel of a precision (item_begin: also a_max)
+cudaError_t record_test_launch(int precision, int n_sub, cudaStream_t stream, const RhsArgs &args, const int *nbr,
+                               const int *rec_uni, const double *rec_val, int *sub_uniform, const int *item_begin);
 
 }  // namespace octh

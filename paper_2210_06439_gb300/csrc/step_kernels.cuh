@@ -328,31 +328,6 @@ __global__ void __launch_bounds__(COMBINE_THREADS, 1) combine_kernel(CombineArgs
         atomicOr(A.flags, 2u);
 }
 
-// The whole-subgrid uniform test of a stage state, derived from the record
-// of the combine that wrote its interiors, right after a uniform-level ghost
-// fill in which every ghost cell has a source: the ghosts of subgrid s copy
-// cells of s itself or of its neighbours, so its ghosted block holds one
-// value per field when s and every neighbour it has took the combine's
-// uniform pass with the same value (bitwise).  A "no" is only conservative.
-__global__ void uniform_from_record_kernel(int n_sub, int nf, const int *nbr, const int *out_uni,
-                                           const double *out_val, int *sub_uniform)
-{
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_sub)
-        return;
-    int uni = out_uni[s];
-    for (int k = 0; k < 26 && uni; k++) {
-        const int t = nbr[26 * (long long)s + k];
-        if (t < 0)
-            continue;
-        uni = out_uni[t];
-        for (int f = 0; f < nf && uni; f++)
-            uni = __double_as_longlong(out_val[(long long)t * MAXNF + f]) ==
-                  __double_as_longlong(out_val[(long long)s * MAXNF + f]);
-    }
-    sub_uniform[s] = uni;
-}
-
 // The ghost shell of a subgrid of edge E, enumerated as: the two z slabs
 // (3 planes of B x B each, lower first), then the two y slabs within the
 // interior z range (3 rows of B each per plane), then the two x slabs within
