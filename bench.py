@@ -135,11 +135,15 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes (read + write) of one launch of the FP64 RHS kernel per
-# workload, from an ncu capture of that kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum) with the kernel as it is now; a workload without an
-# entry reports null.
-RHS_FP64_TRAFFIC = {}
+# DRAM bytes (read + write) of one FP64 RHS call per workload: the uniform
+# test, the work list and the RHS kernel, from ncu captures of the three
+# kernels (dram__bytes_read.sum + dram__bytes_write.sum) as they are now.
+# binary_star_128: measured. binary_star_256: the 128^3 capture scaled per kind
+# of subgrid -- the uniform test reads a uniform subgrid's whole block and
+# writes its RHS, the RHS kernel reads the block of a subgrid left, and each
+# kind grows with its own count (3796 -> 31512 uniform, 300 -> 1256 left).
+# A workload without an entry reports null.
+RHS_FP64_TRAFFIC = {"binary_star_128": 1.138e9, "binary_star_256": 9.38e9}
 
 # The 13 PPM lines (canonical directions).
 LINES = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1), (0, 1, -1),
@@ -488,7 +492,7 @@ def run_ours(args, rank, world):
                      "limiter": bound_of(rhs_tflops / f64_peak, rhs_gbs / hbm_peak),
                      "traffic": RHS_FP64_TRAFFIC.get(args.workload) if args.recon == 0 else None,
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "kernel": "rhs_kernel<double> (FP64 RHS)",
+                     "kernel": "FP64 RHS call: uniform_subgrid_kernel + live_items_kernel + rhs_kernel<double>",
                      "ops_per_cell": ops_eff, "method_ops_per_cell": ops_cell,
                      "ops_note": "FP64 flops of the method's formulas per interior cell, less the work the kernel "
                                  "leaves out: subgrids whose ghosted block holds one value per field (RHS zero, "
