@@ -225,10 +225,20 @@ oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_used_host_out,
  * RK3 steps (or one RHS), copy the result back.  U_host: oct_hydro_state_len
  * doubles (page-locked memory gives full copy speed); dUdt_host:
  * oct_hydro_rhs_len doubles.  The device copy of the state is owned by the
- * handle.  Synchronous. */
+ * handle.  Synchronous.  On a uniform level (periodic or outflow, every ghost
+ * cell with a source) in the default contiguous layout, oct_hydro_rk_steps_host
+ * copies in only the interior z-planes of each field block and fills the
+ * ghosts on the device from the interiors: the step requires U's ghosts to be
+ * those copies anyway, and the ghost layers are most of the state's bytes.
+ * The whole state, ghosts included, is copied back. */
 oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int n_steps, double *dt_last_out,
                                    void *cuda_stream);
 oct_status oct_hydro_rhs_host(oct_hydro_t h, const double *U_host, double *dUdt_host, void *cuda_stream);
+
+/* Bytes oct_hydro_rk_steps_host copies host to device and device to host
+ * per call for the current layout (either pointer may be NULL).  OCT_E_ARG
+ * for a NULL handle or one without a layout. */
+oct_status oct_hydro_host_copy_bytes(oct_hydro_t h, int64_t *h2d_bytes, int64_t *d2h_bytes);
 
 /* Chooses the work decomposition of the RHS kernel for this GPU (Sec. V-B:
  * the paper splits its largest kernels into several tasks so that every

@@ -46,6 +46,7 @@ SIGNATURES = {
     "oct_hydro_rhs_dt_noalloc": (_I, [_I, _I, _I, _D, _I, _D, _D, _P, _P, _P, _P, _P]),
     "oct_hydro_launch_info": (_I, [_P, _P, _P, _P]),
     "oct_hydro_step_launches": (_I, [_P]),
+    "oct_hydro_host_copy_bytes": (_I, [_P, _P, _P]),
     "oct_hydro_gravity_monopole": (_I, [_P, _P, _D, _D, _P, _P, _P]),
     "oct_hydro_pipe_peaks": (_I, [_D, _P, _P, _P]),
     "oct_hydro_eval_math": (_I, [_I, _P, _P, _I64, _D, _P]),
@@ -243,6 +244,12 @@ class Hydro:
         t, c, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(self.L.oct_hydro_launch_info(self.h, ctypes.addressof(t), ctypes.addressof(c), ctypes.addressof(n)))
         return t.value, c.value, n.value
+
+    def host_copy_bytes(self):
+        """(host-to-device, device-to-host) bytes of one rk_steps_host call."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        check(self.L.oct_hydro_host_copy_bytes(self.h, ctypes.addressof(a), ctypes.addressof(b)))
+        return a.value, b.value
 
     def step_launches(self):
         """Kernel launches of one rk_step for the current layout."""

@@ -1236,6 +1236,39 @@ extern "C" oct_status oct_hydro_rk_step(oct_hydro_t h, double *U, double *dt_use
     return OCT_OK;
 }
 
+// Whether the host-buffer step may copy in only the interior z-planes of each
+// field block and refill the ghosts on the device: a uniform level (the
+// ghosts are copies of interior cells, which the step requires of its input
+// anyway) in the default contiguous layout (subgrid s at s nf B^3, so that
+// the runs to copy are evenly spaced and one 2D copy takes them all).
+static bool interior_copy_ok(const oct_hydro *h)
+{
+    if (!(h->bc == OCT_BC_PERIODIC || h->bc == OCT_BC_OUTFLOW) || !h->ghosts_sourced || h->edge.empty())
+        return false;
+    const long long B = h->edge[0] + 2 * NG, block = (long long)h->nf * B * B * B;
+    for (int s = 0; s < h->n_sub; s++)
+        if (h->edge[s] != h->edge[0] || h->off[s] != s * block)
+            return false;
+    return true;
+}
+
+extern "C" oct_status oct_hydro_host_copy_bytes(oct_hydro_t h, int64_t *h2d_bytes, int64_t *d2h_bytes)
+{
+    if (!h || !h->layout_ok)
+        return fail(OCT_E_ARG, "handle is NULL or has no layout");
+    const long long full = (long long)sizeof(double) * h->state_len;
+    long long in = full;
+    if (interior_copy_ok(h)) {
+        const long long E = h->edge[0], B = E + 2 * NG;
+        in = (long long)sizeof(double) * h->n_sub * h->nf * E * B * B;
+    }
+    if (h2d_bytes)
+        *h2d_bytes = in;
+    if (d2h_bytes)
+        *d2h_bytes = full;
+    return OCT_OK;
+}
+
 extern "C" oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int n_steps, double *dt_last_out,
                                               void *cuda_stream)
 {
@@ -1252,7 +1285,18 @@ extern "C" oct_status oct_hydro_rk_steps_host(oct_hydro_t h, double *U_host, int
         CUDA_TRY(cudaMalloc(&h->d_Uhost, sizeof(double) * h->state_len));
     cudaStream_t s = (cudaStream_t)cuda_stream;
     size_t bytes = sizeof(double) * h->state_len;
-    CUDA_TRY(cudaMemcpyAsync(h->d_Uhost, U_host, bytes, cudaMemcpyHostToDevice, s));
+    if (interior_copy_ok(h)) {
+        // the interior z-planes of every field block (one evenly spaced run
+        // each), then the ghosts from the interiors on the device
+        const size_t E = h->edge[0], B = E + 2 * NG, B2 = B * B;
+        const size_t pitch = sizeof(double) * B2 * B;
+        CUDA_TRY(cudaMemcpy2DAsync(h->d_Uhost + NG * B2, pitch, U_host + NG * B2, pitch, sizeof(double) * E * B2,
+                                   (size_t)h->n_sub * h->nf, cudaMemcpyHostToDevice, s));
+        if ((st = launch_ghosts(h, h->d_Uhost, s)) != OCT_OK)
+            return st;
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(h->d_Uhost, U_host, bytes, cudaMemcpyHostToDevice, s));
+    }
     for (int i = 0; i < n_steps; i++)
         if ((st = oct_hydro_rk_step(h, h->d_Uhost, nullptr, cuda_stream)) != OCT_OK)
             return st;

@@ -1220,10 +1220,9 @@ __global__ void __launch_bounds__(UNI_THREADS) uniform_subgrid_kernel(RhsArgs A,
 // subgrids, a block scan gives the positions.  Also zeroes the a_max slots
 // that halves report to by atomic max.
 constexpr int LIVE_THREADS = 1024;
-static __global__ void __launch_bounds__(LIVE_THREADS) live_items_kernel(int n_sub, const int *sub_uniform,
-                                                                  const int *item_begin, const WorkItem *items,
-                                                                  int G, int split, WorkItem *live, int *live_slot,
-                                                                  int *n_live, double *amax_tile)
+static __global__ void __launch_bounds__(LIVE_THREADS)
+    live_items_kernel(int n_sub, const int *sub_uniform, const int *item_begin, const WorkItem *items, int G,
+                      int split, WorkItem *live, int *live_slot, int *n_live, double *amax_tile)
 {
     __shared__ int wsum[LIVE_THREADS / 32];
     __shared__ int s_total;
@@ -1294,10 +1293,9 @@ static __global__ void __launch_bounds__(LIVE_THREADS) live_items_kernel(int n_s
 // each lane loads all fields of two cells at a time (22 loads in flight for
 // 11 fields), the warp votes after each pair of cells.
 constexpr int REC_THREADS = 256;
-static __global__ void __launch_bounds__(REC_THREADS) interior_record_kernel(const double *U, const int *edge,
-                                                                             const long long *off, int nf,
-                                                                             int n_sub, int *rec_uni,
-                                                                             double *rec_val)
+static __global__ void __launch_bounds__(REC_THREADS)
+    interior_record_kernel(const double *U, const int *edge, const long long *off, int nf, int n_sub, int *rec_uni,
+                           double *rec_val)
 {
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * (REC_THREADS / 32) + (threadIdx.x >> 5);

@@ -403,3 +403,37 @@ def test_host_buffer_calls_match_device_calls_bitwise():
     assert torch.equal(dh, d.cpu())
     assert torch.equal(Uh, U.cpu())
     assert H.error_flags() == 0
+
+
+def test_host_step_copies_interior_planes_and_refills_ghosts():
+    """On a uniform level in the contiguous layout, oct_hydro_rk_steps_host
+    copies in only the interior z-planes of each field block and fills the
+    ghosts on the device: a host state whose ghost cells hold NaN steps to
+    the same bits as one with valid ghosts, and as oct_hydro_rk_step on the
+    device.  Another layout (blocks in reverse order) copies the whole
+    state."""
+    torch = _torch()
+    p = oracle_filled(inputs.periodic_box(nsub=2))
+    H = _hydro(p)
+    E, B = 8, 14
+    h2d, d2h = H.host_copy_bytes()
+    assert h2d == p.n_sub * p.nf * E * B * B * 8 and d2h == p.U.nbytes
+    good = torch.from_numpy(p.U.copy()).pin_memory()
+    bad = good.clone().pin_memory()
+    for s in range(p.n_sub):
+        blk = bad[p.off[s]: p.off[s] + p.nf * B ** 3].view(p.nf, B, B, B)
+        blk[:, :3] = float("nan")
+        blk[:, 3 + E:] = float("nan")
+        blk[:, 3:3 + E, :3] = float("nan")
+        blk[:, 3:3 + E, :, 3 + E:] = float("nan")
+    H.rk_steps_host(good, 1)
+    H.rk_steps_host(bad, 1)
+    assert torch.equal(good, bad)
+    U = torch.from_numpy(p.U.copy()).cuda()
+    H.rk_step(U)
+    assert torch.equal(good, U.cpu())
+    assert H.error_flags() == 0
+    q = p.copy()
+    q.off = np.ascontiguousarray(p.off[::-1])
+    Hq = _hydro(q)
+    assert Hq.host_copy_bytes() == (p.U.nbytes, p.U.nbytes)
