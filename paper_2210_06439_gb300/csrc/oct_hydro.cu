@@ -118,6 +118,8 @@ struct oct_hydro {
     int *d_order = nullptr;   // execution order (null: index order)
     int *d_ticket = nullptr;  // dynamic-scheduling counters of the RHS kernel (zero between launches)
     double *d_dtcap = nullptr;  // dt cap of oct_hydro_rk_step (0: none), read by the captured graph
+    double *d_dt_part = nullptr;  // per-block minima of dt_blocks_kernel
+    int *d_dt_count = nullptr;    // its blocks-done counter (zero between launches)
     double *d_amax_tile = nullptr, *d_dt = nullptr, *d_W = nullptr, *d_L = nullptr, *d_Uhost = nullptr,
            *d_Lhost = nullptr;
     unsigned *d_flags = nullptr;
@@ -397,6 +399,12 @@ extern "C" oct_status oct_hydro_create(int n_subgrids, int edge, int ghost, int 
         st = fail(OCT_E_CUDA, "cudaMemset flags");
     if (st == OCT_OK && cudaMalloc(&h->d_dt, sizeof(double)) != cudaSuccess)
         st = fail(OCT_E_NOMEM, "cudaMalloc dt");
+    if (st == OCT_OK && cudaMalloc(&h->d_dt_part, sizeof(double) * DT_MAX_BLOCKS) != cudaSuccess)
+        st = fail(OCT_E_NOMEM, "cudaMalloc dt partial minima");
+    if (st == OCT_OK && cudaMalloc(&h->d_dt_count, sizeof(int)) != cudaSuccess)
+        st = fail(OCT_E_NOMEM, "cudaMalloc dt counter");
+    if (st == OCT_OK && cudaMemset(h->d_dt_count, 0, sizeof(int)) != cudaSuccess)
+        st = fail(OCT_E_CUDA, "cudaMemset dt counter");
     if (st == OCT_OK && cudaMalloc(&h->d_dtcap, sizeof(double)) != cudaSuccess)
         st = fail(OCT_E_NOMEM, "cudaMalloc dt cap");
     if (st == OCT_OK && cudaMemset(h->d_dtcap, 0, sizeof(double)) != cudaSuccess)
@@ -1035,8 +1043,10 @@ extern "C" oct_status oct_hydro_rhs(oct_hydro_t h, const double *U, double *dUdt
 
 static oct_status launch_dt(oct_hydro *h, cudaStream_t s, bool capped = true)
 {
-    dt_kernel<<<1, 1024, 0, s>>>((int)h->items.size(), h->d_items, h->d_dx, h->d_amax_tile, h->cfl,
-                                 capped ? h->d_dtcap : nullptr, h->d_dt);
+    const int n = (int)h->items.size();
+    const int grid = std::max(1, std::min(DT_MAX_BLOCKS, (n + DT_THREADS - 1) / DT_THREADS));
+    dt_blocks_kernel<<<grid, DT_THREADS, 0, s>>>(n, h->d_items, h->d_dx, h->d_amax_tile, h->cfl,
+                                                 capped ? h->d_dtcap : nullptr, h->d_dt_part, h->d_dt_count, h->d_dt);
     CUDA_TRY(cudaGetLastError());
     return OCT_OK;
 }
@@ -1497,6 +1507,8 @@ extern "C" void oct_hydro_destroy(oct_hydro_t h)
     dfree(h->d_flags);
     dfree(h->d_dt);
     dfree(h->d_dtcap);
+    dfree(h->d_dt_part);
+    dfree(h->d_dt_count);
     dfree(h->d_ticket);
     dfree(h->d_gst_off);
     dfree(h->d_gst_k);

@@ -51,6 +51,50 @@ __global__ void dt_kernel(int n_items, const WorkItem *items, const double *dx, 
     }
 }
 
+// dt as dt_kernel gives it, from many blocks: each block takes the min of
+// dx / a_max over a strided share of the items and stores it in part[b];
+// the last block to finish (a counter in device memory, returned to zero
+// for the next launch) takes the min of the parts.  The min does not depend
+// on the order in which the values are combined.
+constexpr int DT_THREADS = 256;
+constexpr int DT_MAX_BLOCKS = 304;  // two per SM of a full GB300
+__global__ void __launch_bounds__(DT_THREADS) dt_blocks_kernel(int n_items, const WorkItem *items, const double *dx,
+                                                               const double *amax_tile, double cfl,
+                                                               const double *dt_cap, double *part, int *count,
+                                                               double *dt)
+{
+    __shared__ double red[DT_THREADS / 32];
+    __shared__ bool last;
+    double m = INFINITY;
+    for (int t = blockIdx.x * DT_THREADS + threadIdx.x; t < n_items; t += gridDim.x * DT_THREADS)
+        m = fmin(m, dx[items[t].s] / amax_tile[t]);
+    for (int o = 16; o > 0; o >>= 1)
+        m = fmin(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < DT_THREADS / 32; w++)
+            m = fmin(m, red[w]);
+        part[blockIdx.x] = m;
+        __threadfence();
+        last = atomicAdd(count, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0)
+        return;
+    __threadfence();
+    double r = INFINITY;
+    for (int b = 0; b < (int)gridDim.x; b++)
+        r = fmin(r, *(volatile double *)(part + b));
+    double d = cfl * r;
+    const double cap = dt_cap ? *dt_cap : 0.0;
+    if (cap > 0.0 && cap < d)
+        d = cap;
+    dt[0] = d;
+    *count = 0;
+}
+
 struct CombineArgs {
     int stage;            // 1, 2, 3
     const double *U0;     // state at the start of the step (ghosted layout)
@@ -373,25 +417,13 @@ struct GhostShell {
 // Ghost cells are enumerated directly (z slabs below and above the interior,
 // then y slabs, then x slabs of the remaining rows); a thread loads all fields
 // of its cell before storing them.
-// With `changed` (per subgrid: its interior may have changed since U's
-// ghosts were last valid), a subgrid whose own and 26 neighbours' interiors
-// are all unchanged keeps its ghosts as they are.
-__global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf, const int *nbr, unsigned *flags,
-                                  const int *changed)
+// The ghost cells of subgrid s, by all threads of the block.
+__device__ __forceinline__ void ghost_fill_block(double *U, int E, const long long *off, int nf, const int *nbr,
+                                                 unsigned *flags, int s)
 {
-    const int s = blockIdx.x;
     const int B = E + 2 * NG;
     const long long FS = (long long)B * B * B;
     const int *nb = nbr + 26 * (long long)s;
-    if (changed != nullptr) {
-        int ch = 0;
-        if (threadIdx.x < 27) {
-            const int t = threadIdx.x == 26 ? s : nb[threadIdx.x];
-            ch = t >= 0 && changed[t] != 0;
-        }
-        if (!__syncthreads_or(ch))
-            return;
-    }
     const GhostShell sh(E);
     bool err = false;
     for (int q = threadIdx.x; q < sh.total; q += blockDim.x) {
@@ -433,6 +465,25 @@ __global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf
     }
     if (err)
         atomicOr(flags, 4u);  // OCT_FLAG_NO_SOURCE
+}
+
+// With `changed` (per subgrid: its interior may have changed since U's
+// ghosts were last valid), a subgrid whose own and 26 neighbours' interiors
+// are all unchanged keeps its ghosts as they are.
+__global__ void ghost_fill_kernel(double *U, int E, const long long *off, int nf, const int *nbr, unsigned *flags,
+                                  const int *changed)
+{
+    const int s = blockIdx.x;
+    if (changed != nullptr) {
+        int ch = 0;
+        if (threadIdx.x < 27) {
+            const int t = threadIdx.x == 26 ? s : nbr[26 * (long long)s + threadIdx.x];
+            ch = t >= 0 && changed[t] != 0;
+        }
+        if (!__syncthreads_or(ch))
+            return;
+    }
+    ghost_fill_block(U, E, off, nf, nbr, flags, s);
 }
 
 // Ghost fill across refinement levels from a host-built plan: entry q of
