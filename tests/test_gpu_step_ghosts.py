@@ -254,3 +254,41 @@ def test_two_states_alternating_on_one_handle():
         chk.U[:] = got
         oracle.ghost_fill(8, chk.off, chk.nf, chk.nbr, chk.U)
         assert np.array_equal(chk.U, got), k
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_state_changed_between_steps(precision):
+    """The uniform box stepped once (which leaves the handle's record of its
+    stage state), then one cell of U perturbed by the caller and the ghosts
+    refilled, then stepped again: the second step must see the change (the
+    disturbed subgrid and its neighbours are no longer uniform), against the
+    oracle, with the ghosts bitwise."""
+    import torch
+    from paper_2210_06439_gb300 import binding
+    p = _uniform_box(1.0)
+    ref = oracle_filled(p)
+    U = torch.from_numpy(ref.U.copy()).cuda()
+    H = binding.Hydro.from_problem(p, precision=precision)
+    oracle.rk3_step(ref.edge, ref.off, ref.dx, ref.nf, ref.U, bc=p.bc, nbr=p.nbr)
+    H.rk_step(U)
+    # perturb the density and energy of one interior cell of subgrid 5, on both sides
+    B = 14
+    for arr in (ref.U,):
+        blk = arr[ref.off[5]: ref.off[5] + ref.nf * B ** 3].reshape(ref.nf, B, B, B)
+        blk[0, 6, 5, 7] *= 1.25
+        blk[4, 6, 5, 7] *= 1.25
+    oracle.ghost_fill(8, ref.off, ref.nf, ref.nbr, ref.U)
+    U.copy_(torch.from_numpy(ref.U))
+    dt_o, _, st = oracle.rk3_step(ref.edge, ref.off, ref.dx, ref.nf, ref.U, bc=p.bc, nbr=p.nbr)
+    assert st == 0
+    dt_g = H.rk_step(U)
+    assert dt_g == pytest.approx(dt_o, rel=1e-12 if precision == 0 else 2e-6)
+    got = U.cpu().numpy()
+    errs = field_errors(interior_layout(got, p), interior_layout(ref.U, p), p.nf, e3s(p))
+    assert np.all(errs <= (1e-12 if precision == 0 else 1e-5)), errs
+    gi = interior_layout(got, p).reshape(p.n_sub, p.nf, -1)
+    assert not np.all(gi[5] == gi[5][:, :1])  # the disturbance is there
+    chk = p.copy()
+    chk.U[:] = got
+    oracle.ghost_fill(8, chk.off, chk.nf, chk.nbr, chk.U)
+    assert np.array_equal(chk.U, got)
