@@ -46,6 +46,7 @@ def test_null_handle_calls_fail_cleanly():
     assert L.oct_hydro_set_params(None, 0, 0.4, 1e-12, 1e-3, 0.1) == binding.OCT_E_ARG
     assert L.oct_hydro_state_len(None) == -1
     assert L.oct_hydro_step_launches(None) == -1
+    assert L.oct_hydro_host_copy_bytes(None, None, None) == binding.OCT_E_ARG
     L.oct_hydro_destroy(None)
 
 
