@@ -76,6 +76,11 @@ struct RhsArgs {
     const WorkItem *live_items;
     const int *live_slot;
     const int *n_live;
+    // optional (null: none): per subgrid, bit f set when field f of its
+    // ghosted block holds one value.  Written by uniform_subgrid_kernel for
+    // every subgrid it tests, read by the FP64 RHS kernel (conserved
+    // reconstruction) for the subgrids that kernel takes
+    unsigned *field_uni;
 };
 
 // q / d for the small divisors of the kernels' index arithmetic (tile widths,

@@ -98,6 +98,9 @@ struct oct_hydro {
     // ghosted block held one value per field ([0..n) the step's state, as of
     // the first stage; [n..2n) the stage state of stages 2 and 3)
     int *d_sub_uniform = nullptr;
+    // per subgrid, by the same test (FP64): the fields whose ghosted block
+    // held one value, for the subgrids the RHS kernel then took
+    unsigned *d_field_uni = nullptr;
     int *d_changed = nullptr;  // per subgrid: interior changed by the last combine (stages 2 and 3)
     bool uni_test = false;     // the last RHS launch ran the uniform test
     // record of the stage state W written by the combines of stages 1 and 2:
@@ -180,6 +183,7 @@ static void free_layout(oct_hydro *h)
     dfree(h->d_nbr);
     dfree(h->d_item_begin);
     dfree(h->d_sub_uniform);
+    dfree(h->d_field_uni);
     dfree(h->d_changed);
     dfree(h->d_out_uni);
     dfree(h->d_out_val);
@@ -312,6 +316,7 @@ static oct_status upload_items(oct_hydro *h)
     dfree(h->d_amax_tile);
     dfree(h->d_order);
     dfree(h->d_sub_uniform);
+    dfree(h->d_field_uni);
     dfree(h->d_changed);
     dfree(h->d_out_uni);
     dfree(h->d_out_val);
@@ -321,6 +326,7 @@ static oct_status upload_items(oct_hydro *h)
     dfree(h->d_live_slot);
     dfree(h->d_n_live);
     CUDA_TRY(cudaMalloc(&h->d_sub_uniform, sizeof(int) * 2 * std::max(1, h->n_sub)));
+    CUDA_TRY(cudaMalloc(&h->d_field_uni, sizeof(unsigned) * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_changed, sizeof(int) * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMalloc(&h->d_out_uni, sizeof(int) * std::max(1, h->n_sub)));
     CUDA_TRY(cudaMemset(h->d_out_uni, 0, sizeof(int) * std::max(1, h->n_sub)));  // W holds nothing known
@@ -961,6 +967,7 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
     A.order = h->d_order;
     A.ticket = h->d_ticket;
     A.sub_uniform = nullptr;
+    A.field_uni = nullptr;
     const int form = form_of(h), mode = h->tile_mode;
     if (h->items_mode != mode || h->items_grid != grid_ctas(h))
         return fail(OCT_E_STATE, "work items were cut for another launch shape");
@@ -969,6 +976,10 @@ static oct_status launch_rhs(oct_hydro *h, const double *U, double *dUdt, cudaSt
         // subgrids whose ghosted block is one value per field: skipped by the
         // RHS kernel
         int *flags = h->d_sub_uniform + (size_t)uni_slot * h->n_sub;
+        // and, in FP64, the fields of each subgrid left that hold one value
+        // (the RHS kernel reconstructs only the others)
+        if (h->precision == 0)
+            A.field_uni = h->d_field_uni;
         if (uni_mode == 2 && record_test_ok(h)) {
             // "yes" from the record; the other subgrids streamed
             CUDA_TRY(record_test_launch(h->precision, h->n_sub, st, A, h->d_nbr, h->d_out_uni, h->d_out_val, flags,
@@ -1764,6 +1775,7 @@ extern "C" oct_status oct_hydro_rhs_dt_noalloc(int n_subgrids, int edge, int n_s
     A.order = nullptr;
     A.ticket = nullptr;
     A.sub_uniform = nullptr;  // the kernel's own per-item uniform test
+    A.field_uni = nullptr;
     A.live_items = nullptr;
     A.live_slot = nullptr;
     A.n_live = nullptr;

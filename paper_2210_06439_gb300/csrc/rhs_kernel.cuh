@@ -399,15 +399,22 @@ __device__ __forceinline__ void sfor(F &&f)
 // arithmetic, and the fields of an item share it (RHS 0.82 -> 0.77 ms on the
 // 64^3 box; two fields 0.78, four 0.82); the FP64 form keeps one field per
 // item (registers).
+//
+// The FP64 form takes only the nfa fields listed in fmap (the others hold one
+// value over the subgrid's whole ghosted block, and their group slots were
+// filled with it once for the item).  Its items read their stencils from the
+// state through L1; with up to 512 threads (128 registers) each thread loads
+// the stencil of its next item before the PPM of the current one, so that the
+// load latency overlaps the arithmetic.
 template <class T, bool STAGED, int G, int NT>
 __device__ __forceinline__ bool phase_a(T *temp, const float *raw, const double *Ub, long long FS, int B, int x0,
                                         int y0, int kz, bool inplane, int nf, int NC, int RWX, int plane,
                                         const int *lists, const int *nlist, const unsigned *magic, const int *so,
-                                        int tid)
+                                        int tid, const unsigned char *fmap, int nfa)
 {
     constexpr int NL = gnl(G);
     constexpr int FPI = STAGED ? 3 : 1;  // fields per item
-    const int nfi = (nf + FPI - 1) / FPI;
+    const int nfi = STAGED ? (nf + FPI - 1) / FPI : nfa;
     // per line: its cell list (the x / y ring only for lines with a nonzero x /
     // y step, in planes that own x / y faces) and its item count; lines without
     // a z step have nothing to do in the boundary planes
@@ -420,6 +427,74 @@ __device__ __forceinline__ bool phase_a(T *temp, const float *raw, const double 
         const int n = inplane ? nlist[t] : (gline(G, L, 2) != 0 ? nlist[0] : 0);
         beg[L + 1] = beg[L] + n * nfi;
     });
+    if constexpr (!STAGED) {
+        // item q: its slot offset o in temp and its stencil (centre ub, step st)
+        auto item = [&](int q, int &o, const double *&ub, long long &st) {
+            sfor<NL>([&](auto Lc) {
+                constexpr int L = decltype(Lc)::value;
+                if (q >= beg[L] && q < beg[L + 1]) {
+                    constexpr int dx = gline(G, L, 0), dy = gline(G, L, 1), dz = gline(G, L, 2);
+                    const int t = inplane ? ((dx != 0) | ((dy != 0) << 1)) : 0;
+                    const int r = q - beg[L];
+                    const int fq = __umulhi((unsigned)r, magic[t]);
+                    const int c = r - fq * nlist[t];
+                    const int info = lists[t * NC + c];
+                    const int i = (info & 0xFF) - 1, j = ((info >> 8) & 0xFF) - 1;
+                    const int f = fmap[fq];
+                    o = ((2 * L) * nf + f) * NC + (info >> 16);
+                    st = (long long)dz * B * B + (long long)dy * B + dx;
+                    ub = Ub + f * FS + (long long)(kz + NG) * B * B + (long long)(y0 + j + NG) * B + (x0 + i + NG);
+                }
+            });
+        };
+        if constexpr (NT <= 512) {
+            double un[5];
+            int on = 0;
+            if (tid < beg[NL]) {
+                const double *ub = Ub;
+                long long st = 0;
+                item(tid, on, ub, st);
+#pragma unroll
+                for (int m = -2; m <= 2; m++)
+                    un[m + 2] = __ldg(ub + m * st);
+            }
+            for (int q = tid; q < beg[NL]; q += NT) {
+                double u[5];
+#pragma unroll
+                for (int m = 0; m < 5; m++)
+                    u[m] = un[m];
+                const int o = on;
+                if (q + NT < beg[NL]) {
+                    const double *ub = Ub;
+                    long long st = 0;
+                    item(q + NT, on, ub, st);
+#pragma unroll
+                    for (int m = -2; m <= 2; m++)
+                        un[m + 2] = __ldg(ub + m * st);
+                }
+                double vm, vp;
+                sawc |= ppm5(u[0], u[1], u[2], u[3], u[4], vm, vp);
+                temp[o] = vm;
+                temp[o + nf * NC] = vp;
+            }
+        } else {
+            for (int q = tid; q < beg[NL]; q += NT) {
+                int o = 0;
+                const double *ub = Ub;
+                long long st = 0;
+                item(q, o, ub, st);
+                double u[5];
+#pragma unroll
+                for (int m = -2; m <= 2; m++)
+                    u[m + 2] = __ldg(ub + m * st);
+                double vm, vp;
+                sawc |= ppm5(u[0], u[1], u[2], u[3], u[4], vm, vp);
+                temp[o] = vm;
+                temp[o + nf * NC] = vp;
+            }
+        }
+        return sawc;
+    }
     for (int q = tid; q < beg[NL]; q += NT) {
         sfor<NL>([&](auto Lc) {
             constexpr int L = decltype(Lc)::value;
@@ -528,6 +603,12 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
     __shared__ int s_const[2];
     if (tid < 2)
         s_const[tid] = 0;
+    // FP64, conserved reconstruction: the fields of the item that phase A
+    // reconstructs (those not one value over the subgrid's ghosted block)
+    constexpr bool FSKIP = sizeof(T) == 8 && !STAGED && !PRIM;
+    __shared__ unsigned char s_fmap[MAXNF];
+    if (tid < MAXNF)
+        s_fmap[tid] = (unsigned char)tid;
     const int n_items = A.n_live != nullptr ? A.n_live[0] : A.n_items;
     for (int k = blockIdx.x; k < n_items;) {
         const int it = A.n_live != nullptr ? k : (A.order != nullptr ? A.order[k] : k);
@@ -684,6 +765,28 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
             }
         }
         if (!ucol) {
+        unsigned funi = 0u;  // fields whose whole ghosted block holds one value
+        if constexpr (FSKIP) {
+            if (A.field_uni != nullptr)
+                funi = A.field_uni[s] & ((1u << nf) - 1u);
+            if (tid == 0) {
+                int k = 0;
+                for (int f = 0; f < nf; f++)
+                    if (!((funi >> f) & 1u))
+                        s_fmap[k++] = (unsigned char)f;
+            }
+            if (funi != 0u) {
+                // every stencil of such a field is constant: its point values are
+                // its one value, in every group slot for the whole item (phase A
+                // writes only the other fields' slots)
+                for (int q = tid; q < 8 * nf * NC; q += NT) {
+                    const int sf = q / NC, f = sf - (sf / nf) * nf;
+                    if ((funi >> f) & 1u)
+                        temp[q] = __ldg(Ub + f * FS);
+                }
+            }
+        }
+        const int nfa = nf - __popc(funi);
         for (int kz = -3; kz <= 1; kz++)
             stage_plane(kz);
         __syncthreads();
@@ -719,7 +822,7 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
 #define OCT_PHASE_A(GG)                                                                                              \
     case GG:                                                                                                         \
         sawc = phase_a<T, STAGED, GG, NT>(temp, raw, Ub, FS, B, x0, y0, kz, inplane, nf, NC, RWX, RWY * RWX, lists,     \
-                                          nlist, magic, so, tid);                                                    \
+                                          nlist, magic, so, tid, s_fmap, nfa);                                       \
         break;
                     OCT_PHASE_A(0)
                     OCT_PHASE_A(1)
@@ -754,7 +857,7 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
                         }
                     }
                 }
-                if (sawc)
+                if (sawc || funi != 0u)
                     s_const[g & 1] = 1;
                 __syncthreads();
                 const bool gconst = s_const[g & 1] != 0;
@@ -1167,21 +1270,28 @@ __global__ void __launch_bounds__(UNI_THREADS) uniform_subgrid_kernel(RhsArgs A,
     const int n2 = B * B * B / 2;  // B is even: whole double2 per field
     const double *Ub = A.U + A.off[s];
     const int nf = A.nf;
-    int diff = 0;
-    for (int f = 0; f < nf && !diff; f++) {
+    // fields found to differ; with a per-field record wanted every field is
+    // tested, else the test leaves at the first field that differs
+    unsigned fdiff = 0u;
+    for (int f = 0; f < nf && (fdiff == 0u || A.field_uni != nullptr); f++) {
         const double *fb = Ub + (long long)f * 2 * n2;
         const double2 *f2 = reinterpret_cast<const double2 *>(fb);
         const double ref = __ldg(fb);
+        int diff = 0;
 #pragma unroll 4
         for (int v = tid; v < n2; v += UNI_THREADS) {
             const double2 w = __ldg(f2 + v);
             diff |= (bit_diff(w.x, ref) | bit_diff(w.y, ref)) != 0u;
         }
-        diff = __syncthreads_or(diff);
+        if (__syncthreads_or(diff))
+            fdiff |= 1u << f;
     }
-    if (diff) {
-        if (tid == 0)
+    if (fdiff != 0u) {
+        if (tid == 0) {
             sub_uniform[s] = 0;
+            if (A.field_uni != nullptr)
+                A.field_uni[s] = ~fdiff & ((1u << nf) - 1u);
+        }
         return;
     }
     const T gamma = Num<T>::from_d(A.gamma);
