@@ -494,48 +494,40 @@ __device__ __forceinline__ bool phase_a(T *temp, const float *raw, const double 
             }
         }
         return sawc;
-    }
-    for (int q = tid; q < beg[NL]; q += NT) {
-        sfor<NL>([&](auto Lc) {
-            constexpr int L = decltype(Lc)::value;
-            if (q >= beg[L] && q < beg[L + 1]) {
-                constexpr int dx = gline(G, L, 0), dy = gline(G, L, 1), dz = gline(G, L, 2);
-                const int t = inplane ? ((dx != 0) | ((dy != 0) << 1)) : 0;
-                const int n = nlist[t];
-                const int r = q - beg[L];
-                const int fq = __umulhi((unsigned)r, magic[t]);
-                const int c = r - fq * n;
-                const int info = lists[t * NC + c];
-                const int i = (info & 0xFF) - 1, j = ((info >> 8) & 0xFF) - 1, ci = info >> 16;
+    } else {
+        for (int q = tid; q < beg[NL]; q += NT) {
+            sfor<NL>([&](auto Lc) {
+                constexpr int L = decltype(Lc)::value;
+                if (q >= beg[L] && q < beg[L + 1]) {
+                    constexpr int dx = gline(G, L, 0), dy = gline(G, L, 1), dz = gline(G, L, 2);
+                    const int t = inplane ? ((dx != 0) | ((dy != 0) << 1)) : 0;
+                    const int n = nlist[t];
+                    const int r = q - beg[L];
+                    const int fq = __umulhi((unsigned)r, magic[t]);
+                    const int c = r - fq * n;
+                    const int info = lists[t * NC + c];
+                    const int i = (info & 0xFF) - 1, j = ((info >> 8) & 0xFF) - 1, ci = info >> 16;
 #pragma unroll
-                for (int k = 0; k < FPI; k++) {
-                    const int f = FPI * fq + k;
-                    if (k > 0 && f >= nf)
-                        break;
-                    T u[5];
-                    if constexpr (STAGED) {
+                    for (int k = 0; k < FPI; k++) {
+                        const int f = FPI * fq + k;
+                        if (k > 0 && f >= nf)
+                            break;
+                        T u[5];
                         const float *rb = raw + f * plane + (j + NG) * RWX + (i + NG);
                         const int step = dy * RWX + dx;
 #pragma unroll
                         for (int m = -2; m <= 2; m++)
                             u[m + 2] = (T)rb[so[dz > 0 ? m + 2 : (dz < 0 ? 2 - m : 2)] + m * step];
-                    } else {
-                        const long long st = (long long)dz * B * B + (long long)dy * B + dx;
-                        const double *ub =
-                            Ub + f * FS + (long long)(kz + NG) * B * B + (long long)(y0 + j + NG) * B + (x0 + i + NG);
-#pragma unroll
-                        for (int m = -2; m <= 2; m++)
-                            u[m + 2] = Num<T>::from_d(__ldg(ub + m * st));
+                        T vm, vp;
+                        sawc |= ppm5(u[0], u[1], u[2], u[3], u[4], vm, vp);
+                        temp[((2 * L) * nf + f) * NC + ci] = vm;
+                        temp[((2 * L + 1) * nf + f) * NC + ci] = vp;
                     }
-                    T vm, vp;
-                    sawc |= ppm5(u[0], u[1], u[2], u[3], u[4], vm, vp);
-                    temp[((2 * L) * nf + f) * NC + ci] = vm;
-                    temp[((2 * L + 1) * nf + f) * NC + ci] = vp;
                 }
-            }
-        });
+            });
+        }
+        return sawc;
     }
-    return sawc;
 }
 
 // PRIM: the state array holds the primitive variables w of every cell
@@ -604,11 +596,17 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
     if (tid < 2)
         s_const[tid] = 0;
     // FP64, conserved reconstruction: the fields of the item that phase A
-    // reconstructs (those not one value over the subgrid's ghosted block)
+    // reconstructs (those not one value over the subgrid's ghosted block).
+    // Not in the FP32 form: it is issue-bound, and looking the fields up in
+    // the staging and the PPM items cost more there than the fields skipped
+    // save (mixed RHS 0.76 -> 0.84 ms on the box, 2.92 -> 2.97 ms on the
+    // 256^3 binary star)
     constexpr bool FSKIP = sizeof(T) == 8 && !STAGED && !PRIM;
     __shared__ unsigned char s_fmap[MAXNF];
     if (tid < MAXNF)
         s_fmap[tid] = (unsigned char)tid;
+    unsigned cur_funi = 0u;  // the fields s_fmap leaves out
+    __syncthreads();
     const int n_items = A.n_live != nullptr ? A.n_live[0] : A.n_items;
     for (int k = blockIdx.x; k < n_items;) {
         const int it = A.n_live != nullptr ? k : (A.order != nullptr ? A.order[k] : k);
@@ -634,6 +632,22 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
         const unsigned m_rc = rcp_div(rows_s * cols_s), m_cols = rcp_div(cols_s);
         const int ncin = tx * ty;
         double amax = 0.0;
+        unsigned funi = 0u;  // fields whose whole ghosted block holds one value
+        if constexpr (FSKIP) {
+            if (A.field_uni != nullptr)
+                funi = A.field_uni[s] & ((1u << nf) - 1u);
+            if (funi != cur_funi) {  // the same for the whole CTA
+                if (tid == 0) {
+                    int k = 0;
+                    for (int f = 0; f < nf; f++)
+                        if (!((funi >> f) & 1u))
+                            s_fmap[k++] = (unsigned char)f;
+                }
+                __syncthreads();
+                cur_funi = funi;
+            }
+        }
+        const int nfa = nf - __popc(funi);  // fields phase A takes: s_fmap[0 .. nfa)
         // this subgrid's boundary face fluxes, if wanted (looked up where used:
         // a pointer kept live across the plane loop costs registers)
         auto face_block = [&]() -> double * {
@@ -765,28 +779,17 @@ __global__ void __launch_bounds__(NT, MINB) rhs_kernel(RhsArgs A)
             }
         }
         if (!ucol) {
-        unsigned funi = 0u;  // fields whose whole ghosted block holds one value
-        if constexpr (FSKIP) {
-            if (A.field_uni != nullptr)
-                funi = A.field_uni[s] & ((1u << nf) - 1u);
-            if (tid == 0) {
-                int k = 0;
-                for (int f = 0; f < nf; f++)
-                    if (!((funi >> f) & 1u))
-                        s_fmap[k++] = (unsigned char)f;
-            }
-            if (funi != 0u) {
-                // every stencil of such a field is constant: its point values are
-                // its one value, in every group slot for the whole item (phase A
-                // writes only the other fields' slots)
-                for (int q = tid; q < 8 * nf * NC; q += NT) {
-                    const int sf = q / NC, f = sf - (sf / nf) * nf;
-                    if ((funi >> f) & 1u)
-                        temp[q] = __ldg(Ub + f * FS);
-                }
+        if (funi != 0u) {
+            // every stencil of such a field is constant, and PPM returns a
+            // constant stencil's value unchanged: its point values are its one
+            // value, in every group slot for the whole item (phase A writes only
+            // the other fields' slots)
+            for (int q = tid; q < 8 * nf * NC; q += NT) {
+                const int sf = q / NC, f = sf - (sf / nf) * nf;
+                if ((funi >> f) & 1u)
+                    temp[q] = Num<T>::from_d(__ldg(Ub + f * FS));
             }
         }
-        const int nfa = nf - __popc(funi);
         for (int kz = -3; kz <= 1; kz++)
             stage_plane(kz);
         __syncthreads();

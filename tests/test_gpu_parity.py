@@ -169,6 +169,60 @@ def test_binary_star_small(precision):
     _check_rhs(inputs.binary_star(nsub=4), precision)
 
 
+def test_fp64_fields_of_one_value_are_skipped_exactly(tmp_path, monkeypatch):
+    """The 32^3 binary star in FP64: in the subgrids the stellar surfaces cut
+    through, some fields (z momentum, the species of the other star) hold one
+    value over the whole ghosted block, and the handle's RHS reconstructs
+    only the other fields. Every stencil of such a field is constant, so
+    skipping it must change no bit. So the RHS of every launch shape equals,
+    bitwise, that of the allocation-free call (whose kernel has no such
+    record and reconstructs every field), and the oracle's within 1e-12."""
+    torch = _torch()
+    from paper_2210_06439_gb300 import binding
+    p = oracle_filled(inputs.binary_star(nsub=4))
+    nf, E = p.nf, 8
+    skipped = 0
+    for s in range(p.n_sub):
+        b = p.block(s).reshape(nf, -1).view(np.int64)
+        one = np.all(b == b[:, :1], axis=1)
+        if not one.all():
+            skipped += int(one.sum())
+    assert skipped > 0
+    U = torch.from_numpy(p.U).cuda()
+    L = binding.load()
+    dx = torch.from_numpy(np.ascontiguousarray(p.dx)).cuda()
+    ref = torch.full((p.n_sub * nf * E ** 3,), float("nan"), dtype=torch.float64, device="cuda")
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = L.oct_hydro_rhs_dt_noalloc(p.n_sub, E, p.n_species, p.gamma, 0, 0.4, 1e-3, U.data_ptr(), dx.data_ptr(),
+                                    ref.data_ptr(), dt.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert st == binding.OCT_OK
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    d_o, _, _ = oracle.rhs(p.edge, p.off, p.dx, p.nf, p.U)
+    assert np.all(field_errors(ref, d_o, nf, e3s(p)) <= TOL[0])
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("OCT_HYDRO_TUNE_CACHE", str(path))
+    H = _hydro(p, 0)
+    path.write_text("")
+    H.autotune(U)
+    key = path.read_text().split()[0]
+    seen = set()
+    for mode in range(4):
+        path.write_text(f"{key} {mode} 1\n")
+        H.autotune(U)
+        if H.launch_info()[:2] != (mode, 1):
+            continue
+        seen.add(mode)
+        d = torch.zeros(H.rhs_len, dtype=torch.float64, device="cuda")
+        H.rhs(U, d)
+        torch.cuda.synchronize()
+        assert H.error_flags() == 0
+        got = d.cpu().numpy()
+        assert np.array_equal(got.view(np.int64), ref.view(np.int64)), (mode, np.flatnonzero(got != ref)[:8])
+    assert seen == {0, 1, 2, 3}, seen
+    H.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_uniform_subgrids_take_the_whole_block_test(precision):
     """The 32^3 binary star (64 subgrids, 48 of them atmosphere): the
