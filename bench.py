@@ -138,14 +138,14 @@ def _peaks():
 # DRAM bytes (read + write) of one FP64 RHS call per workload: the uniform
 # test, the work list and the RHS kernel, from ncu captures of the three
 # kernels (dram__bytes_read.sum + dram__bytes_write.sum) as they are now.
-# binary_star_128: measured (uniform test 990.9 MB read + 147.2 MB written,
-# work list 0.04 MB, RHS kernel 57.7 MB). binary_star_256: the 128^3 capture
+# binary_star_128: measured (uniform test 990.9 MB read + 147.0 MB written,
+# work list 0.04 MB, RHS kernel 57.6 MB). binary_star_256: the 128^3 capture
 # scaled per kind of subgrid -- the uniform test reads every subgrid's whole
 # block and writes the RHS of the uniform ones, the RHS kernel reads the block
 # of a subgrid left, and each kind grows with its own count (4096 -> 32768
 # blocks, 3796 -> 31512 uniform, 300 -> 1256 left).  A workload without an
 # entry reports null.
-RHS_FP64_TRAFFIC = {"binary_star_128": 1.196e9, "binary_star_256": 9.39e9}
+RHS_FP64_TRAFFIC = {"binary_star_128": 1.195e9, "binary_star_256": 9.39e9}
 
 # The 13 PPM lines (canonical directions).
 LINES = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1), (0, 1, -1),
